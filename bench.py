@@ -1,0 +1,330 @@
+"""Benchmark: seconds per RHMC trajectory on a 32^3x8 lattice (mixed precision
+vs plain FP64, both solved to 1e-10), plus the Dslash roofline.
+
+Workload (one "step" = one trajectory through the whole hot path: heatbath
+with r_{1/4}, action with r_{-1/2}, Omelyan MD with gauge and fermion forces,
+FP64 link and momentum updates, Metropolis):
+  32^3x8, beta = 5.5, m = 0.0075, one pseudofermion, degree-15 rationals on
+  [1e-5, 64] from the library's Remez, Omelyan 2MN, tau = 1, 20 steps,
+  solver tolerance 1e-10, links exp(i 0.3 H) with H Gaussian (seed 1 + rank).
+Multi-GPU: the path does not shard (one lattice per GPU), so N ranks run N
+independent replicas (different seeds) and the value is the whole-job
+seconds per trajectory: max-over-ranks time / (steps * N).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DIMS = (32, 32, 32, 8)
+BETA, MASS, TAU, NSTEPS, DEG, LO, HI, TOL = 5.5, 0.0075, 1.0, 20, 15, 1e-5, 64.0, 1e-10
+ROOF_DIMS = (64, 64, 64, 16)  # working set >= 4x L2 for the Dslash roofline
+# total multi-shift iterations of one FP64 trajectory of this workload, as
+# counted by the library's FP64 path (identical to the oracle's recursion);
+# used to scale the oracle's per-iteration cost to a trajectory
+REF_ITERS_PER_TRAJ = int(os.environ.get("STAG_REF_ITERS", "0")) or None
+WORKLOAD = "rhmc_32x32x32x8_omelyan20_deg15_m0.0075"
+
+
+def _metric():
+    return "s/trajectory (RHMC 32^3x8, 1e-10 residual)"
+
+
+def _params(stag, rat_hb, rat_act, mode, traj, seed):
+    return stag.make_params(BETA, MASS, TAU, NSTEPS, stag.INT_OMELYAN, rat_hb, rat_act, rat_act,
+                            tol_md=TOL, tol_metro=TOL, mode_md=mode, mode_metro=mode, seed=seed,
+                            traj=traj)
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd += ["-i", uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        rows = [r.split(", ") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_uuid(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def hop_roofline(stag, torch, dims, nrep=30):
+    """Average duration of the FP32 D_oe hop (12-real FP32 links), each launch
+    timed with CUDA events on the launching stream after an L2 flush.
+    Algorithmic bytes per output site: 8 links x 48 B + 8 neighbours x 24 B
+    + 1 output x 24 B = 600 B."""
+    from paper_1106_5673_gb300 import synth
+    L = stag.Lattice(dims)
+    L.load_gauge(synth.near_unit_links(dims, 0.3, 5))
+    x = torch.from_numpy(synth.gaussian_vector(dims, 6)).cuda().to(torch.complex64)
+    y = L.vector(stag.PREC_F32)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        L.apply_doe(x, y, stag.PREC_F32)
+    times = []
+    for _ in range(nrep):
+        flush.fill_(1.0)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        L.apply_doe(x, y, stag.PREC_F32)
+        b.record()
+        b.synchronize()
+        times.append(a.elapsed_time(b) * 1e-3)
+    L.close()
+    t = statistics.mean(times)
+    Vh = int(np.prod(dims)) // 2
+    return {"seconds": t, "bytes": 600.0 * Vh, "gbs": 600.0 * Vh / t / 1e9,
+            "gflops": 570.0 * Vh / t / 1e9, "dims": list(dims)}
+
+
+def cpu_sample(U, rat_act, iters_per_traj, n_force):
+    """The FP64 oracle on the host: a bounded sample of the trajectory's work,
+    scaled to seconds per trajectory."""
+    import oracle as O
+    from paper_1106_5673_gb300 import synth
+    O.build()
+    dims = DIMS
+    a0, a, b = rat_act
+    phi = synth.gaussian_vector(dims, 7)
+    t0 = time.perf_counter()
+    nit = 6
+    _, _, tot, _ = O.multishift(dims, U, MASS, np.array(b), phi, tol=1e-30, maxit=nit)
+    t_iter = (time.perf_counter() - t0) / max(tot, 1)
+    t0 = time.perf_counter()
+    O.gauge_force(dims, U, BETA)
+    t_gf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.fermion_force(dims, U, MASS, a0, a, b, phi, tol=1e-30, maxit=1)
+    t_ff = time.perf_counter() - t0 - t_iter  # one solver iteration inside
+    w = synth.gaussian_momenta(dims, 8)
+    t0 = time.perf_counter()
+    O.update_links(dims, U, w, 0.01)
+    t_up = time.perf_counter() - t0
+    est = iters_per_traj * t_iter + n_force * (t_gf + t_ff) + 2 * NSTEPS * t_up
+    return {"value": est, "unit": "s/trajectory", "cores": 1, "kind": "oracle",
+            "sample": ("oracle FP64 on 32^3x8: %d multi-shift iterations (15 shifts), 1 gauge "
+                       "force, 1 fermion-force assembly, 1 link update, timed on 1 host core and "
+                       "scaled by %d iterations and %d force evaluations per trajectory"
+                       % (nit, iters_per_traj, n_force)),
+            "parts_s": {"iter": t_iter, "gauge_force": t_gf, "fermion_force": t_ff,
+                        "link_update": t_up}}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1106_5673_gb300 import synth
+    # the oracle's own Remez output (written by tests/golden/make_rationals.py)
+    with open(os.path.join(ROOT, "tests", "golden", "rationals.json")) as f:
+        gold = json.load(f)
+    r = gold["p-1/2_d15_1e-5"]
+    rat = (r["a0"], r["a"], r["b"])
+    iters = REF_ITERS_PER_TRAJ or args.ref_iters
+    U = synth.near_unit_links(DIMS, 0.3, 1)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        s = cpu_sample(U, rat, iters, 2 * NSTEPS + 1)
+        if i >= args.warmup:
+            vals.append(s)
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": _metric(), "value": v, "unit": "s/trajectory",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS)},
+            "cpu_baseline": {"value": v, "unit": "s/trajectory", "cores": 1, "kind": "oracle",
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "s/trajectory", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--ref-iters", type=int, default=50000)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1106_5673_gb300 import stag, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    a0, a, b, err_act = stag.remez(-0.5, LO, HI, DEG)
+    h0, ha, hb, err_hb = stag.remez(0.25, LO, HI, DEG)
+    rat_act, rat_hb = (a0, a, b), (h0, ha, hb)
+    U0 = synth.near_unit_links(DIMS, 0.3, 1 + rank)
+    L = stag.Lattice(DIMS)
+    L.load_gauge(U0)
+
+    # warm-up trajectories (untimed), then K timed ones: mixed precision
+    for i in range(args.warmup):
+        L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED, i, 100 + rank))
+    n0 = L.launch_count()
+    clocks = ClockSampler(_gpu_uuid(torch, local))
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    infos = []
+    for k in range(args.steps):
+        infos.append(L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED,
+                                             args.warmup + k, 100 + rank)))
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    ck = clocks.stop()
+    t = e0.elapsed_time(e1) * 1e-3
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    launches = L.launch_count() - n0
+    value = t / (args.steps * world)
+    iters_mixed = sum(i["cg_iters"] for i in infos) / len(infos)
+
+    # plain FP64 GPU form of the same trajectory (same start, same random numbers)
+    fp64 = None
+    if not args.no_fp64:
+        L2 = stag.Lattice(DIMS)
+        L2.load_gauge(L.store_gauge())
+        traj = args.warmup + args.steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        i64 = L2.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_F64, traj, 100 + rank))
+        t64 = time.perf_counter() - t0
+        im = L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED, traj, 100 + rank))
+        fp64 = {"s_per_traj": t64, "cg_iters": i64["cg_iters"], "dH": i64["dH"],
+                "accepted": i64["accepted"], "mixed_dH_same_start": im["dH"],
+                "mixed_accepted_same_start": im["accepted"], "speedup_mixed": t64 / value
+                if world == 1 else None}
+        L2.close()
+
+    # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
+    Uh = L.store_gauge()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L.load_gauge(Uh)
+    L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED, 999, 100 + rank))
+    Uh = L.store_gauge()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
+
+    roof = hop_roofline(stag, torch, DIMS)
+    roof_large = hop_roofline(stag, torch, ROOF_DIMS)
+    peak, peak_kind = _peaks()
+
+    line = {
+        "metric": _metric(), "value": value, "unit": "s/trajectory", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "beta": BETA, "mass": MASS,
+                   "integrator": "omelyan", "nsteps": NSTEPS, "tau": TAU, "rational_degree": DEG,
+                   "rational_range": [LO, HI], "rational_err": [err_act, err_hb], "tol": TOL,
+                   "solver": "mixed: fp32 multishift + fp64 reliable-update refinement",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set > L2 (links fp64+fp32+bf16 ~176 MB, solver vectors ~200 MB)"},
+        "roofline": {"bound": "hbm", "achieved": roof["gbs"], "peak": peak, "unit": "GB/s",
+                     "frac": roof["gbs"] / peak, "traffic": None,
+                     "kernel": "k_hop<float,LP32> (D_oe, FP32 12-real links)",
+                     "dims": roof["dims"], "peak_kind": peak_kind},
+        "roofline_large": {"bound": "hbm", "achieved": roof_large["gbs"], "peak": peak,
+                           "unit": "GB/s", "frac": roof_large["gbs"] / peak,
+                           "dims": roof_large["dims"], "gflops": roof_large["gflops"]},
+        "e2e": {"value": t_e2e, "unit": "s/trajectory", "h2d_bytes_per_step": link_bytes,
+                "d2h_bytes_per_step": link_bytes},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "trajectories": [{k: i[k] for k in ("dH", "accepted", "plaq", "cg_iters", "n_force",
+                                             "t_md", "t_total")} for i in infos],
+        "cg_iters_per_traj_mixed": iters_mixed,
+        "fp64_compare": fp64,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        iters = fp64["cg_iters"] if fp64 else (REF_ITERS_PER_TRAJ or args.ref_iters)
+        line["cpu_baseline"] = cpu_sample(U0, rat_act, iters, infos[0]["n_force"])
+    if rank == 0:
+        print(json.dumps(line))
+    L.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

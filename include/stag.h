@@ -1,0 +1,233 @@
+/*
+ * stag.h -- C ABI of the GB300 staggered-RHMC library (libstag.so).
+ *
+ * Two-flavour staggered RHMC as described in C. Bonati, G. Cossu, M. D'Elia,
+ * P. Incardona, "QCD simulations with staggered fermions on GPUs"
+ * (arXiv:1106.5673): the even/odd staggered operator of Eq. (4), the shifted
+ * (multi-shift) CG of Eq. (13) that applies the RHMC rational functions
+ * (Sec. 2.1), the gauge and fermion forces, the SU(3) momentum and link
+ * update and the Metropolis test, with a whole molecular-dynamics trajectory
+ * kept on one GPU (Sec. 4).
+ *
+ * Conventions
+ *  - Every function returns an int status: STAG_OK (0) or a negative
+ *    STAG_ERR_* code; stag_last_error(ctx) gives a message owned by the
+ *    library.  The library never aborts and never traps the device; every
+ *    device-side loop is bounded.
+ *  - Lattice: dims = {Lx, Ly, Lz, Lt}, each even and >= 2; V = Lx Ly Lz Lt,
+ *    Vh = V/2.  Site n = (x,y,z,t) has lex = x + Lx*(y + Ly*(z + Lz*t)),
+ *    parity (x+y+z+t) mod 2, and index lex/2 within its parity.  Fermions are
+ *    antiperiodic in t, links periodic in all directions.
+ *  - Canonical host/device layouts at this boundary:
+ *      gauge    complex128 [4][V][3][3]  (mu = 0..3 = x,y,z,t; row-major)
+ *      vector   complex    [Vh][3]       sites of one parity; complex128
+ *                                        for STAG_PREC_F64, complex64
+ *                                        (float re/im) for F32 and BF16
+ *      momenta  float64    [4][V][8]     Gell-Mann coefficients w^a of
+ *                                        P = sum_a w^a lambda^a / 2
+ *    Internally the library keeps its own structure-of-arrays forms.
+ *  - Pointers are borrowed: the caller owns them (usually PyTorch tensors)
+ *    and keeps them alive until the stream has been synchronised.  Device
+ *    pointers must be 16-byte aligned.  Objects created by stag_*_create are
+ *    owned by the library and freed by the matching destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless documented as
+ *    synchronising.
+ */
+#ifndef STAG_H
+#define STAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    STAG_OK = 0,
+    STAG_ERR_ARG = -1,       /* invalid argument (null pointer, bad size, bad mode)   */
+    STAG_ERR_CUDA = -2,      /* a CUDA runtime call failed                             */
+    STAG_ERR_NOCONV = -3,    /* a solver hit its iteration cap above tolerance         */
+    STAG_ERR_NONFINITE = -4, /* NaN/Inf found in a result that must be finite          */
+    STAG_ERR_OOM = -5,       /* device allocation failed                               */
+    STAG_ERR_STATE = -6      /* call out of order (e.g. no gauge field loaded)         */
+};
+
+enum { STAG_PREC_F64 = 0, STAG_PREC_F32 = 1, STAG_PREC_BF16 = 2 };
+
+/* Solver modes: plain FP64, or FP32/BF16 bulk with FP64 reliable updates and
+ * an FP64 true-residual check of every shift. */
+enum { STAG_SOLVE_F64 = 0, STAG_SOLVE_MIXED = 1, STAG_SOLVE_MIXED_BF16 = 2 };
+
+enum { STAG_INT_LEAPFROG = 0, STAG_INT_OMELYAN = 1 };
+
+#define STAG_MAXSHIFT 32
+#define STAG_MAXPF 8
+
+typedef struct stag_ctx stag_ctx;
+
+/* r(x) = a0 + sum_{k<n} a[k] / (x + b[k]): the RHMC rational function
+ * (Sec. 2.1), b[k] > 0 the shifts of Eq. (13). */
+typedef struct {
+    double a0;
+    int n;
+    double a[STAG_MAXSHIFT];
+    double b[STAG_MAXSHIFT];
+} stag_rational;
+
+typedef struct {
+    int status;                          /* STAG_OK or STAG_ERR_NOCONV             */
+    int iters;                           /* multi-shift (base) iterations           */
+    int iters_shift[STAG_MAXSHIFT];      /* iterations each shift was updated       */
+    int refine_iters[STAG_MAXSHIFT];     /* single-shift refinement iterations      */
+    double true_resid[STAG_MAXSHIFT];    /* |b - (M+s_k) x_k| / |b| in FP64         */
+    int reliable_updates;                /* FP64 residual replacements performed    */
+    int matvecs;                         /* M_ee applications of any precision      */
+} stag_solve_info;
+
+typedef struct {
+    double beta, mass, tau;
+    int nsteps;                 /* MD steps of size tau/nsteps                      */
+    int integrator;             /* STAG_INT_LEAPFROG or STAG_INT_OMELYAN           */
+    double lambda;              /* Omelyan 2MN parameter (0.1931833275037836)       */
+    int npf;                    /* pseudofermions, 1..STAG_MAXPF                    */
+    stag_rational hb;           /* r ~ x^{+1/(4 npf)}  heatbath                     */
+    stag_rational act;          /* r ~ x^{-1/(2 npf)}  action (Metropolis)          */
+    stag_rational force;        /* r ~ x^{-1/(2 npf)}  molecular dynamics           */
+    double tol_md, tol_metro;   /* relative residuals of MD and Metropolis solves   */
+    int solve_mode_md;          /* STAG_SOLVE_* for the force solves                */
+    int solve_mode_metro;       /* STAG_SOLVE_* for heatbath and action solves      */
+    int maxit;                  /* iteration cap of every solve                     */
+    uint32_t seed, traj;        /* Philox key (seed, traj)                          */
+    int use_graphs;             /* capture the MD loop's force/update steps         */
+} stag_params;
+
+typedef struct {
+    double H0, H1, dH, u;       /* Hamiltonians, their difference, Metropolis u    */
+    int accepted;
+    double plaq;                /* average plaquette after the accept/reject        */
+    long long cg_iters;         /* multi-shift + refinement iterations              */
+    int n_force;                /* force evaluations                                */
+    double t_heatbath, t_action, t_md, t_total; /* seconds (host wall clock)        */
+    int status;
+} stag_traj_info;
+
+/* ---------------- context ---------------- */
+
+/* Creates a context for one lattice on the current CUDA device and allocates
+ * its device storage (gauge field in FP64/FP32/BF16 12-real form, momenta,
+ * solver work space sized on first use).  dims as above. */
+int stag_ctx_create(const int dims[4], stag_ctx **out);
+int stag_ctx_destroy(stag_ctx *ctx);
+const char *stag_last_error(const stag_ctx *ctx);
+/* Bytes of device memory held by the context. */
+int stag_ctx_device_bytes(const stag_ctx *ctx, size_t *bytes);
+/* Number of CUDA kernels the context has launched so far (kernels inside
+ * captured graphs counted one by one); for accounting in benchmarks. */
+int stag_ctx_launch_count(const stag_ctx *ctx, long long *n);
+
+/* ---------------- fields ---------------- */
+
+/* Loads the gauge field (canonical layout, complex128, host or device pointer;
+ * on_device selects which) and builds the internal FP64, FP32 and BF16 copies
+ * holding the first two rows of each link (the third is rebuilt as the
+ * conjugate cross product, Sec. 4.2).  Links must be SU(3). */
+int stag_load_gauge(stag_ctx *ctx, const double *links, int on_device, void *stream);
+/* Writes the gauge field back in the canonical layout. */
+int stag_store_gauge(stag_ctx *ctx, double *links, int on_device, void *stream);
+int stag_load_momenta(stag_ctx *ctx, const double *w, int on_device, void *stream);
+int stag_store_momenta(stag_ctx *ctx, double *w, int on_device, void *stream);
+/* Average plaquette (1/6V) sum Re Tr U_P / 3 in FP64.  Synchronises. */
+int stag_plaquette(stag_ctx *ctx, double *plaq, void *stream);
+/* Wilson gauge action beta sum_P (1 - Re Tr U_P / 3).  Synchronises. */
+int stag_gauge_action(stag_ctx *ctx, double beta, double *action, void *stream);
+
+/* ---------------- operator (Eq. (4), a = 1) ---------------- */
+
+/* out_even = D_eo in_odd:  (D psi)(n) = 1/2 sum_mu eta_mu(n) [U_mu(n) psi(n+mu)
+ * - U_mu(n-mu)^dag psi(n-mu)].  Device vectors in the canonical layout of
+ * `prec` (F64: complex128; F32, BF16: complex64, with FP32 resp. BF16 links). */
+int stag_apply_deo(stag_ctx *ctx, const void *in_odd, void *out_even, int prec, void *stream);
+/* out_odd = D_oe in_even. */
+int stag_apply_doe(stag_ctx *ctx, const void *in_even, void *out_odd, int prec, void *stream);
+/* out_even = M_ee in_even = m^2 in - D_eo D_oe in  (even/odd preconditioned
+ * M^dag M, Sec. 2.1).  in and out must not alias. */
+int stag_apply_M(stag_ctx *ctx, double mass, const void *in_even, void *out_even, int prec,
+                 void *stream);
+
+/* ---------------- solvers (Sec. 4.3, Eq. (13)) ---------------- */
+
+/* Solves (M_ee + shifts[k]) x_k = src for k < n (1 <= n <= STAG_MAXSHIFT,
+ * shifts >= 0) from x = 0 with the shifted CG, stopping shift k when its
+ * residual falls below tol*|src|.  src and sols[k] are FP64 device vectors
+ * (canonical complex128, even sites); sols[k] may alias nothing else.
+ * mode: STAG_SOLVE_F64, or STAG_SOLVE_MIXED(_BF16): FP32 multi-shift with FP64
+ * reliable updates of the base residual, then an FP64-reliable-update CG per
+ * shift started from x_k until the FP64 true residual meets tol.  The true
+ * residual of every shift is computed in FP64 and returned in info.
+ * Synchronises (reads convergence flags).  Returns STAG_ERR_NOCONV if any
+ * shift misses tol within maxit iterations. */
+int stag_multishift_solve(stag_ctx *ctx, double mass, int n, const double *shifts,
+                          const double *src, double *const *sols, double tol, int maxit,
+                          int mode, stag_solve_info *info, void *stream);
+
+/* out = r(M_ee) src = a0 src + sum_k a_k (M_ee + b_k)^{-1} src (RHMC, Sec. 2.1).
+ * FP64 device vectors; out may not alias src.  Synchronises. */
+int stag_rational_apply(stag_ctx *ctx, double mass, const stag_rational *r, const double *src,
+                        double *out, double tol, int maxit, int mode, stag_solve_info *info,
+                        void *stream);
+
+/* ---------------- forces and updates ---------------- */
+
+/* Gauge force dP/dtau = (i beta/6) TA(U_mu(n) A_mu(n)) of the Wilson action
+ * (A = sum of the six staples, TA = traceless anti-Hermitian part) as
+ * Gell-Mann coefficients, canonical momenta layout, FP64 device array. */
+int stag_gauge_force(stag_ctx *ctx, double beta, double *force_out, void *stream);
+
+/* Fermion force of S_f = phi^dag r(M_ee) phi: with X_k = (M_ee+b_k)^{-1} phi
+ * and Y_k = D_oe X_k, dP/dtau = i TA(W), W = (eta/2) U sum_k a_k Z_k,
+ * Z_k = X_k(n+mu) Y_k(n)^dag (n odd) or -Y_k(n+mu) X_k(n)^dag (n even).
+ * phi: FP64 device vector (even sites); force_out: canonical momenta layout.
+ * Synchronises (solver). */
+int stag_fermion_force(stag_ctx *ctx, double mass, const stag_rational *r, const double *phi,
+                       double *force_out, double tol, int maxit, int mode,
+                       stag_solve_info *info, void *stream);
+
+/* Link update U <- exp(i eps P) U with the context's momenta, in FP64, then
+ * reunitarisation (Sec. 4.1) and refresh of the FP32/BF16 copies. */
+int stag_update_links(stag_ctx *ctx, double eps, void *stream);
+
+/* Philox4x32-10 momentum heatbath into the context's momenta: w^a ~ N(0,1)
+ * with counter (1, mu, lex, block) and key (seed, traj). */
+int stag_momenta_heatbath(stag_ctx *ctx, uint32_t seed, uint32_t traj, void *stream);
+
+/* Complex Gaussian R (density exp(-R^dag R)) on even sites, counter
+ * (2, pf, lex, colour) and key (seed, traj); out is an FP64 device vector. */
+int stag_pf_gaussian(stag_ctx *ctx, uint32_t seed, uint32_t traj, int pf, double *out,
+                     void *stream);
+
+/* Kinetic term sum Tr P^2 = 1/2 sum w^2 of the context's momenta.  Synchronises. */
+int stag_kinetic(stag_ctx *ctx, double *out, void *stream);
+
+/* ---------------- trajectory (Sec. 2.1, Fig. traj_fig) ---------------- */
+
+/* One RHMC trajectory on the device: momentum and pseudofermion heatbath
+ * (phi = r_hb(M) R per pseudofermion), H0, MD over tau with the chosen
+ * integrator, H1, Metropolis with u from Philox counter (3,0,0,0); on
+ * rejection the gauge field is restored.  Synchronises. */
+int stag_md_trajectory(stag_ctx *ctx, const stag_params *p, stag_traj_info *out, void *stream);
+
+/* ---------------- host helper ---------------- */
+
+/* Best relative rational approximation of x^power on [lo, hi] of type
+ * (degree, degree) by the Remez exchange, as partial fractions.  Host only,
+ * needs no GPU.  degree <= STAG_MAXSHIFT. */
+int stag_remez(double power, double lo, double hi, int degree, stag_rational *out,
+               double *max_rel_err);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STAG_H */

@@ -1,0 +1,399 @@
+// lattice.cuh -- device-side geometry, complex/SU(3) arithmetic and the
+// internal structure-of-arrays layouts of the GB300 staggered library.
+//
+// Internal layouts (all arrays 16-byte aligned, Vh = V/2 sites per parity):
+//   links, FP64  double2 [mu][parity][6][Vh]   rows 0,1 of U_mu(n): u00 u01 u02 u10 u11 u12
+//   links, FP32  float4  [mu][parity][3][Vh]   (u00,u01) (u02,u10) (u11,u12)
+//   links, BF16  uint2   [mu][parity][3][Vh]   same pairs, 4 bf16 per 8 bytes
+//   momenta      double  [mu][parity][8][Vh]   Gell-Mann coefficients w^a
+//   vectors      complex [Vh][3]               canonical, AoS (same as the C ABI)
+// The third link row is rebuilt on the fly as conj(row0 x row1), which holds
+// for SU(3) (12-real storage of Sec. 4.2).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#define STAG_HD __host__ __device__ __forceinline__
+#define STAG_D __device__ __forceinline__
+
+struct Geom {
+    int L[4];
+    int V, Vh;
+    int Lx2;  // Lx/2, the x-extent in half-site units
+};
+
+// ---------------------------------------------------------------- complex
+
+template <typename R> struct Cplx { R re, im; };
+typedef Cplx<double> cd;
+typedef Cplx<float> cf;
+
+template <typename R> STAG_HD Cplx<R> cmk(R a, R b) { Cplx<R> c; c.re = a; c.im = b; return c; }
+template <typename R> STAG_HD Cplx<R> operator+(Cplx<R> a, Cplx<R> b) { return cmk(a.re + b.re, a.im + b.im); }
+template <typename R> STAG_HD Cplx<R> operator-(Cplx<R> a, Cplx<R> b) { return cmk(a.re - b.re, a.im - b.im); }
+template <typename R> STAG_HD Cplx<R> operator*(Cplx<R> a, Cplx<R> b) {
+    return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <typename R> STAG_HD Cplx<R> operator*(R s, Cplx<R> a) { return cmk(s * a.re, s * a.im); }
+template <typename R> STAG_HD Cplx<R> conj(Cplx<R> a) { return cmk(a.re, -a.im); }
+// a^* b
+template <typename R> STAG_HD Cplx<R> cjmul(Cplx<R> a, Cplx<R> b) {
+    return cmk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+template <typename R> STAG_HD R norm2(Cplx<R> a) { return a.re * a.re + a.im * a.im; }
+
+// colour vector and 3x3 matrix
+template <typename R> struct Vec3 { Cplx<R> c[3]; };
+template <typename R> struct Mat3 { Cplx<R> e[3][3]; };
+
+template <typename R> STAG_HD Vec3<R> vzero() {
+    Vec3<R> v;
+#pragma unroll
+    for (int i = 0; i < 3; i++) v.c[i] = cmk<R>(0, 0);
+    return v;
+}
+
+// rebuild row 2 = conj(row0 x row1) (SU(3), det = 1)
+template <typename R> STAG_HD void recon_row2(Mat3<R>& u) {
+    u.e[2][0] = conj(u.e[0][1] * u.e[1][2] - u.e[0][2] * u.e[1][1]);
+    u.e[2][1] = conj(u.e[0][2] * u.e[1][0] - u.e[0][0] * u.e[1][2]);
+    u.e[2][2] = conj(u.e[0][0] * u.e[1][1] - u.e[0][1] * u.e[1][0]);
+}
+
+template <typename R> STAG_HD Mat3<R> mmul(const Mat3<R>& a, const Mat3<R>& b) {
+    Mat3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            c.e[i][j] = a.e[i][0] * b.e[0][j] + a.e[i][1] * b.e[1][j] + a.e[i][2] * b.e[2][j];
+    return c;
+}
+// a^dag b
+template <typename R> STAG_HD Mat3<R> mdmul(const Mat3<R>& a, const Mat3<R>& b) {
+    Mat3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            c.e[i][j] = cjmul(a.e[0][i], b.e[0][j]) + cjmul(a.e[1][i], b.e[1][j]) +
+                        cjmul(a.e[2][i], b.e[2][j]);
+    return c;
+}
+// a b^dag
+template <typename R> STAG_HD Mat3<R> mmuld(const Mat3<R>& a, const Mat3<R>& b) {
+    Mat3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++)
+            c.e[i][j] = cjmul(b.e[j][0], a.e[i][0]) + cjmul(b.e[j][1], a.e[i][1]) +
+                        cjmul(b.e[j][2], a.e[i][2]);
+    return c;
+}
+template <typename R> STAG_HD Mat3<R> madd(const Mat3<R>& a, const Mat3<R>& b) {
+    Mat3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) c.e[i][j] = a.e[i][j] + b.e[i][j];
+    return c;
+}
+template <typename R> STAG_HD Mat3<R> mzero() {
+    Mat3<R> c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) c.e[i][j] = cmk<R>(0, 0);
+    return c;
+}
+
+// ---------------------------------------------------------------- Hermitian / algebra
+// P = sum_a w^a lambda^a / 2 (Gell-Mann), as the 3x3 matrix
+//   P00 = (w3 + w8/sqrt3)/2, P11 = (-w3 + w8/sqrt3)/2, P22 = -w8/sqrt3,
+//   P01 = (w1 - i w2)/2, P02 = (w4 - i w5)/2, P12 = (w6 - i w7)/2.
+#define STAG_INV_SQRT3 0.57735026918962576451
+
+STAG_HD Mat3<double> omega_to_herm(const double w[8]) {
+    Mat3<double> P;
+    const double s = STAG_INV_SQRT3;
+    P.e[0][0] = cmk(0.5 * (w[2] + w[7] * s), 0.0);
+    P.e[1][1] = cmk(0.5 * (-w[2] + w[7] * s), 0.0);
+    P.e[2][2] = cmk(-w[7] * s, 0.0);
+    P.e[0][1] = cmk(0.5 * w[0], -0.5 * w[1]);
+    P.e[1][0] = cmk(0.5 * w[0], 0.5 * w[1]);
+    P.e[0][2] = cmk(0.5 * w[3], -0.5 * w[4]);
+    P.e[2][0] = cmk(0.5 * w[3], 0.5 * w[4]);
+    P.e[1][2] = cmk(0.5 * w[5], -0.5 * w[6]);
+    P.e[2][1] = cmk(0.5 * w[5], 0.5 * w[6]);
+    return P;
+}
+
+// For W, returns the Gell-Mann coefficients f^a of i TA(W) = sum_a f^a lambda^a/2,
+// TA(W) = (W - W^dag)/2 - Tr(W - W^dag)/6.  With A = TA(W) anti-Hermitian
+// traceless, i A is Hermitian and f^a = Tr(i A lambda^a).
+STAG_HD void i_ta_to_omega(const Mat3<double>& W, double f[8]) {
+    // A_ij = (W_ij - conj(W_ji))/2 - trace part;  (iA)_ij = i A_ij
+    // f1 = 2 Re (iA)_01, f2 = -2 Im (iA)_01 ... written out from Tr(iA lambda^a)
+    const double a01r = 0.5 * (W.e[0][1].re - W.e[1][0].re), a01i = 0.5 * (W.e[0][1].im + W.e[1][0].im);
+    const double a02r = 0.5 * (W.e[0][2].re - W.e[2][0].re), a02i = 0.5 * (W.e[0][2].im + W.e[2][0].im);
+    const double a12r = 0.5 * (W.e[1][2].re - W.e[2][1].re), a12i = 0.5 * (W.e[1][2].im + W.e[2][1].im);
+    // diagonal of A is i*Im(W_kk) minus i*tr/3
+    const double d0 = W.e[0][0].im, d1 = W.e[1][1].im, d2 = W.e[2][2].im;
+    const double tr = (d0 + d1 + d2) / 3.0;
+    const double h0 = -(d0 - tr), h1 = -(d1 - tr);  // (iA)_kk = i * i (d_k - tr) = -(d_k - tr)
+    // (iA)_01 = i (a01r + i a01i) = -a01i + i a01r ; (iA)_10 = conj
+    // Tr(iA lambda1) = (iA)_01 + (iA)_10 = 2 Re (iA)_01 = -2 a01i
+    // Tr(iA lambda2) = i (iA)_01 - i (iA)_10 = -2 Im (iA)_01 = -2 a01r
+    f[0] = -2.0 * a01i;
+    f[1] = -2.0 * a01r;
+    f[2] = h0 - h1;
+    f[3] = -2.0 * a02i;
+    f[4] = -2.0 * a02r;
+    f[5] = -2.0 * a12i;
+    f[6] = -2.0 * a12r;
+    // Tr(iA lambda8) = (h0 + h1 - 2 h2)/sqrt3, h2 = -h0 - h1
+    f[7] = (h0 + h1 - 2.0 * (-h0 - h1)) * STAG_INV_SQRT3;
+}
+
+// ---------------------------------------------------------------- geometry
+
+struct Site {
+    int x[4];
+    int lex;
+};
+
+// site of parity `par` with index h (lex/2): lex is 2h or 2h+1
+STAG_D Site site_of(const Geom& g, int h, int par) {
+    Site s;
+    int lex0 = 2 * h;
+    int x0 = lex0 % g.L[0];
+    int r = lex0 / g.L[0];
+    s.x[1] = r % g.L[1];
+    r /= g.L[1];
+    s.x[2] = r % g.L[2];
+    s.x[3] = r / g.L[2];
+    int p0 = (x0 + s.x[1] + s.x[2] + s.x[3]) & 1;
+    s.x[0] = x0 + (p0 != par);
+    s.lex = lex0 + (p0 != par);
+    return s;
+}
+
+// lex of the neighbour n + dir mu
+STAG_D int nb_lex(const Geom& g, const Site& s, int mu, int dir) {
+    int stride = 1;
+#pragma unroll
+    for (int m = 0; m < 4; m++) {
+        if (m == mu) {
+            int xm = s.x[m] + dir;
+            int delta = dir;
+            if (xm == g.L[m]) delta = 1 - g.L[m];
+            if (xm < 0) delta = g.L[m] - 1;
+            return s.lex + delta * stride;
+        }
+        stride *= g.L[m];
+    }
+    return s.lex;
+}
+
+// staggered phase eta_mu(n) = (-1)^(x_0 + ... + x_{mu-1}) as +-1
+STAG_D int eta(const Site& s, int mu) {
+    int t = 0;
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+        if (m < mu) t += s.x[m];
+    return (t & 1) ? -1 : 1;
+}
+
+// ---------------------------------------------------------------- link loads
+
+STAG_D Mat3<double> load_link64(const double2* __restrict__ U, const Geom& g, int mu, int par, int h) {
+    const double2* p = U + (size_t)(mu * 2 + par) * 6 * g.Vh + h;
+    Mat3<double> u;
+    double2 a0 = __ldg(p), a1 = __ldg(p + g.Vh), a2 = __ldg(p + 2 * (size_t)g.Vh);
+    double2 a3 = __ldg(p + 3 * (size_t)g.Vh), a4 = __ldg(p + 4 * (size_t)g.Vh), a5 = __ldg(p + 5 * (size_t)g.Vh);
+    u.e[0][0] = cmk(a0.x, a0.y); u.e[0][1] = cmk(a1.x, a1.y); u.e[0][2] = cmk(a2.x, a2.y);
+    u.e[1][0] = cmk(a3.x, a3.y); u.e[1][1] = cmk(a4.x, a4.y); u.e[1][2] = cmk(a5.x, a5.y);
+    recon_row2(u);
+    return u;
+}
+
+STAG_D Mat3<float> load_link32(const float4* __restrict__ U, const Geom& g, int mu, int par, int h) {
+    const float4* p = U + (size_t)(mu * 2 + par) * 3 * g.Vh + h;
+    float4 a = __ldg(p), b = __ldg(p + g.Vh), c = __ldg(p + 2 * (size_t)g.Vh);
+    Mat3<float> u;
+    u.e[0][0] = cmk(a.x, a.y); u.e[0][1] = cmk(a.z, a.w);
+    u.e[0][2] = cmk(b.x, b.y); u.e[1][0] = cmk(b.z, b.w);
+    u.e[1][1] = cmk(c.x, c.y); u.e[1][2] = cmk(c.z, c.w);
+    recon_row2(u);
+    return u;
+}
+
+STAG_D float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+STAG_D float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+STAG_D Mat3<float> load_link16(const uint2* __restrict__ U, const Geom& g, int mu, int par, int h) {
+    const uint2* p = U + (size_t)(mu * 2 + par) * 3 * g.Vh + h;
+    uint2 a = __ldg(p), b = __ldg(p + g.Vh), c = __ldg(p + 2 * (size_t)g.Vh);
+    Mat3<float> u;
+    u.e[0][0] = cmk(bf_lo(a.x), bf_hi(a.x)); u.e[0][1] = cmk(bf_lo(a.y), bf_hi(a.y));
+    u.e[0][2] = cmk(bf_lo(b.x), bf_hi(b.x)); u.e[1][0] = cmk(bf_lo(b.y), bf_hi(b.y));
+    u.e[1][1] = cmk(bf_lo(c.x), bf_hi(c.x)); u.e[1][2] = cmk(bf_lo(c.y), bf_hi(c.y));
+    recon_row2(u);
+    return u;
+}
+
+STAG_D void store_link64(double2* U, const Geom& g, int mu, int par, int h, const Mat3<double>& u) {
+    double2* p = U + (size_t)(mu * 2 + par) * 6 * g.Vh + h;
+    p[0] = make_double2(u.e[0][0].re, u.e[0][0].im);
+    p[g.Vh] = make_double2(u.e[0][1].re, u.e[0][1].im);
+    p[2 * (size_t)g.Vh] = make_double2(u.e[0][2].re, u.e[0][2].im);
+    p[3 * (size_t)g.Vh] = make_double2(u.e[1][0].re, u.e[1][0].im);
+    p[4 * (size_t)g.Vh] = make_double2(u.e[1][1].re, u.e[1][1].im);
+    p[5 * (size_t)g.Vh] = make_double2(u.e[1][2].re, u.e[1][2].im);
+}
+
+STAG_D uint32_t pack_bf2(float lo, float hi) {
+    __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// write the low-precision copies of one link from its FP64 rows 0,1
+STAG_D void store_link_lowp(float4* U32, uint2* U16, const Geom& g, int mu, int par, int h,
+                            const Mat3<double>& u) {
+    size_t base = (size_t)(mu * 2 + par) * 3 * g.Vh + h;
+    float v[12] = {(float)u.e[0][0].re, (float)u.e[0][0].im, (float)u.e[0][1].re, (float)u.e[0][1].im,
+                   (float)u.e[0][2].re, (float)u.e[0][2].im, (float)u.e[1][0].re, (float)u.e[1][0].im,
+                   (float)u.e[1][1].re, (float)u.e[1][1].im, (float)u.e[1][2].re, (float)u.e[1][2].im};
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        U32[base + (size_t)j * g.Vh] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        U16[base + (size_t)j * g.Vh] = make_uint2(pack_bf2(v[4 * j], v[4 * j + 1]),
+                                                  pack_bf2(v[4 * j + 2], v[4 * j + 3]));
+    }
+}
+
+// ---------------------------------------------------------------- vector loads (AoS)
+
+STAG_D Vec3<double> load_vec(const double2* __restrict__ v, int h) {
+    const double2* p = v + 3 * (size_t)h;
+    double2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    Vec3<double> r;
+    r.c[0] = cmk(a.x, a.y); r.c[1] = cmk(b.x, b.y); r.c[2] = cmk(c.x, c.y);
+    return r;
+}
+STAG_D Vec3<float> load_vec(const float2* __restrict__ v, int h) {
+    const float2* p = v + 3 * (size_t)h;
+    float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    Vec3<float> r;
+    r.c[0] = cmk(a.x, a.y); r.c[1] = cmk(b.x, b.y); r.c[2] = cmk(c.x, c.y);
+    return r;
+}
+// non-cached-path load for buffers written earlier by the same kernel sequence
+STAG_D Vec3<double> ld_vec(const double2* v, int h) {
+    const double2* p = v + 3 * (size_t)h;
+    double2 a = p[0], b = p[1], c = p[2];
+    Vec3<double> r;
+    r.c[0] = cmk(a.x, a.y); r.c[1] = cmk(b.x, b.y); r.c[2] = cmk(c.x, c.y);
+    return r;
+}
+STAG_D Vec3<float> ld_vec(const float2* v, int h) {
+    const float2* p = v + 3 * (size_t)h;
+    float2 a = p[0], b = p[1], c = p[2];
+    Vec3<float> r;
+    r.c[0] = cmk(a.x, a.y); r.c[1] = cmk(b.x, b.y); r.c[2] = cmk(c.x, c.y);
+    return r;
+}
+STAG_D void st_vec(double2* v, int h, const Vec3<double>& r) {
+    double2* p = v + 3 * (size_t)h;
+    p[0] = make_double2(r.c[0].re, r.c[0].im);
+    p[1] = make_double2(r.c[1].re, r.c[1].im);
+    p[2] = make_double2(r.c[2].re, r.c[2].im);
+}
+STAG_D void st_vec(float2* v, int h, const Vec3<float>& r) {
+    float2* p = v + 3 * (size_t)h;
+    p[0] = make_float2(r.c[0].re, r.c[0].im);
+    p[1] = make_float2(r.c[1].re, r.c[1].im);
+    p[2] = make_float2(r.c[2].re, r.c[2].im);
+}
+
+// U psi and U^dag psi
+template <typename R> STAG_D Vec3<R> mv(const Mat3<R>& u, const Vec3<R>& v) {
+    Vec3<R> r;
+#pragma unroll
+    for (int a = 0; a < 3; a++) r.c[a] = u.e[a][0] * v.c[0] + u.e[a][1] * v.c[1] + u.e[a][2] * v.c[2];
+    return r;
+}
+template <typename R> STAG_D Vec3<R> mdv(const Mat3<R>& u, const Vec3<R>& v) {
+    Vec3<R> r;
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+        r.c[a] = cjmul(u.e[0][a], v.c[0]) + cjmul(u.e[1][a], v.c[1]) + cjmul(u.e[2][a], v.c[2]);
+    return r;
+}
+
+// ---------------------------------------------------------------- reductions
+
+STAG_D double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-wide sum of one double (blockDim.x multiple of 32, <= 1024); result valid in thread 0
+STAG_D double block_sum(double v) {
+    __shared__ double red_smem[32];
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red_smem[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (w == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        s = (lane < nw) ? red_smem[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+// ---------------------------------------------------------------- shared helpers
+
+STAG_D Site site_from_lex(const Geom& g, int lex) {
+    Site s;
+    s.lex = lex;
+    s.x[0] = lex % g.L[0];
+    int r = lex / g.L[0];
+    s.x[1] = r % g.L[1];
+    r /= g.L[1];
+    s.x[2] = r % g.L[2];
+    s.x[3] = r / g.L[2];
+    return s;
+}
+STAG_D int par_of(const Site& s) { return (s.x[0] + s.x[1] + s.x[2] + s.x[3]) & 1; }
+STAG_D int par_of_lex(const Geom& g, int lex) { return par_of(site_from_lex(g, lex)); }
+
+// last-block-done: returns true in exactly one block, after all blocks have
+// written their partials (threadfence + counter), and resets the counter.
+STAG_D bool last_block(unsigned int* counter) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (am_last && threadIdx.x == 0) *counter = 0;
+    return am_last;
+}
+
+// sum of partials[0..n) into *dst by block 0 style loop in the last block
+STAG_D void finish_sum(const double* partials, int n, double* dst) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += __ldcg(partials + i);
+    s = block_sum(s);
+    if (threadIdx.x == 0) *dst = s;
+}
+

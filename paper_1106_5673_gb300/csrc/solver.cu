@@ -1,0 +1,717 @@
+// solver.cu -- shifted (multi-shift) CG for (M_ee + s_k) x_k = b (Eq. (13),
+// Sec. 4.3) and the single-shift CG with FP64 reliable updates used to refine
+// each shift in mixed precision.
+//
+// One iteration of the shifted CG is four kernels:
+//   A  t   = D_oe p                                   (hop, odd output)
+//   B  w   = c0 p - D_eo t, pw = Re<p,w>              (hop, even output, fused
+//          reduction; the last block computes alpha, zeta^{j+1}_k, a_k)
+//   C  r  -= alpha w, rr = |r|^2                      (last block: beta, b_k,
+//          convergence per shift, stop flag)
+//   D  p   = r + beta p; x_k += a_k p_k; p_k = zeta_k r + b_k p_k
+// All scalars live in device memory (MSState), so the host never waits inside
+// an iteration; it reads the `live` flag every `chunk` iterations.  The chunk
+// is captured once per context as a CUDA graph.  Kernels started after the
+// stop flag return immediately.
+#include "hop.cuh"
+#include "stag_internal.h"
+
+#include <chrono>
+#include <math.h>
+#include <stdlib.h>
+
+static const int HOP_TPB = 128;
+static const int BLAS_TPB = 256;
+
+static int env_int(const char* name, int dflt) {
+    const char* v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+static double env_dbl(const char* name, double dflt) {
+    const char* v = getenv(name);
+    return v ? atof(v) : dflt;
+}
+
+// ============================================================== multi-shift kernels
+
+template <typename R, int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_ms_A(Geom g, const void* __restrict__ U,
+                                                  const typename VT<R>::T* __restrict__ p,
+                                                  typename VT<R>::T* __restrict__ t, const int* live) {
+    if (!*live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= g.Vh) return;
+    const Site s = site_of(g, h, 1);
+    Vec3<R> acc = hop2<R, LP>(g, U, p, h, 1, s);
+#pragma unroll
+    for (int a = 0; a < 3; a++) acc.c[a] = (R)0.5 * acc.c[a];
+    st_vec(t, h, acc);
+}
+
+// w = c0 p - 1/2 hop(t) on even sites; returns Re<p, w> in FP64 via partials
+template <typename R, int LP>
+STAG_D double mee_second_hop(const Geom& g, const void* U, const typename VT<R>::T* t,
+                             const typename VT<R>::T* p, typename VT<R>::T* w, R c0, int h) {
+    double pw = 0.0;
+    if (h < g.Vh) {
+        const Site s = site_of(g, h, 0);
+        Vec3<R> acc = hop2<R, LP>(g, U, t, h, 0, s);
+        Vec3<R> pv = load_vec(p, h);
+        Vec3<R> r;
+        R ppw = 0;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            r.c[a] = c0 * pv.c[a] - (R)0.5 * acc.c[a];
+            ppw += pv.c[a].re * r.c[a].re + pv.c[a].im * r.c[a].im;
+        }
+        st_vec(w, h, r);
+        pw = (double)ppw;
+    }
+    return pw;
+}
+
+template <typename R, int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_ms_B(Geom g, const void* __restrict__ U,
+                                                  const typename VT<R>::T* __restrict__ t,
+                                                  const typename VT<R>::T* __restrict__ p,
+                                                  typename VT<R>::T* __restrict__ w, MSState* st, double* partials,
+                                                  unsigned int* counter) {
+    if (!st->live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    double pw = mee_second_hop<R, LP>(g, U, t, p, w, (R)st->c0, h);
+    pw = block_sum(pw);
+    if (threadIdx.x == 0) partials[blockIdx.x] = pw;
+    if (last_block(counter)) {
+        double tot = 0.0;
+        for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + i);
+        tot = block_sum(tot);
+        if (threadIdx.x == 0) {
+            st->pw = tot;
+            const double alpha = st->rr / tot;
+            st->alpha = alpha;
+            const double s0 = st->shifts[st->base];
+            for (int k = 0; k < st->n; k++) {
+                if (st->active[k]) {
+                    const double d = st->shifts[k] - s0;
+                    const double den = st->zeta_old[k] * st->alpha_old * (1.0 + d * alpha) +
+                                       alpha * st->beta_old * (st->zeta_old[k] - st->zeta[k]);
+                    const double zn = st->zeta[k] * st->zeta_old[k] * st->alpha_old / den;
+                    st->zeta_next[k] = zn;
+                    st->ak[k] = alpha * zn / st->zeta[k];
+                    st->upd_x[k] = 1;
+                } else {
+                    st->upd_x[k] = 0;
+                    st->ak[k] = 0.0;
+                }
+            }
+        }
+    }
+}
+
+template <typename V2, typename R>
+__global__ void k_ms_C(long n, V2* __restrict__ r, const V2* __restrict__ w, MSState* st, double* partials,
+                       unsigned int* counter) {
+    if (!st->live) return;
+    const R alpha = (R)st->alpha;
+    double acc = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        V2 rv = r[i], wv = w[i];
+        rv.x -= alpha * wv.x;
+        rv.y -= alpha * wv.y;
+        r[i] = rv;
+        acc += (double)(rv.x * rv.x + rv.y * rv.y);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (last_block(counter)) {
+        double tot = 0.0;
+        for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + i);
+        tot = block_sum(tot);
+        if (threadIdx.x == 0) {
+            const double rr_new = tot;
+            st->iter += 1;
+            const double beta = rr_new / st->rr;
+            int n_active = 0;
+            for (int k = 0; k < st->n; k++) {
+                if (st->upd_x[k]) {
+                    const double ratio = st->zeta_next[k] / st->zeta[k];
+                    st->bk[k] = beta * ratio * ratio;
+                    st->zeta_old[k] = st->zeta[k];
+                    st->zeta[k] = st->zeta_next[k];
+                    st->iters_shift[k] = st->iter;
+                    st->active[k] = (st->zeta[k] * st->zeta[k] * rr_new > st->tol2bb) ? 1 : 0;
+                }
+                n_active += st->active[k];
+            }
+            st->n_active = n_active;
+            st->beta = beta;
+            st->rr = rr_new;
+            st->alpha_old = st->alpha;
+            st->beta_old = beta;
+            const int bad = !isfinite(rr_new) || !isfinite(beta);
+            if (bad) st->nonfinite = 1;
+            st->stop_next = (n_active == 0 || st->iter >= st->maxit || bad) ? 1 : 0;
+        }
+    }
+}
+
+template <typename V2, typename R>
+__global__ void k_ms_D(long n, long stride, const V2* __restrict__ r, V2* __restrict__ p, V2* __restrict__ pk,
+                       V2* __restrict__ xk, MSState* st, unsigned int* counter) {
+    if (!st->live) return;
+    __shared__ R s_ak[STAG_MAXSHIFT], s_bk[STAG_MAXSHIFT], s_z[STAG_MAXSHIFT];
+    __shared__ int s_ux[STAG_MAXSHIFT], s_act[STAG_MAXSHIFT];
+    const int ns = st->n;
+    if (threadIdx.x < ns) {
+        s_ak[threadIdx.x] = (R)st->ak[threadIdx.x];
+        s_bk[threadIdx.x] = (R)st->bk[threadIdx.x];
+        s_z[threadIdx.x] = (R)st->zeta[threadIdx.x];
+        s_ux[threadIdx.x] = st->upd_x[threadIdx.x];
+        s_act[threadIdx.x] = st->active[threadIdx.x];
+    }
+    __syncthreads();
+    const R beta = (R)st->beta;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const V2 rv = r[i];
+        V2 pv = p[i];
+        pv.x = rv.x + beta * pv.x;
+        pv.y = rv.y + beta * pv.y;
+        p[i] = pv;
+        for (int k = 0; k < ns; k++) {
+            if (!s_ux[k]) continue;
+            V2 q = pk[k * stride + i];
+            V2 x = xk[k * stride + i];
+            x.x += s_ak[k] * q.x;
+            x.y += s_ak[k] * q.y;
+            xk[k * stride + i] = x;
+            if (s_act[k]) {
+                q.x = s_z[k] * rv.x + s_bk[k] * q.x;
+                q.y = s_z[k] * rv.y + s_bk[k] * q.y;
+                pk[k * stride + i] = q;
+            }
+        }
+    }
+    if (last_block(counter)) {
+        if (threadIdx.x == 0 && st->stop_next) st->live = 0;
+    }
+}
+
+// initial vectors: r = p = p_k = b, x_k = 0 (b in FP64, vectors in V2)
+template <typename V2>
+__global__ void k_ms_init_vec(long n, long stride, int ns, const double2* __restrict__ b, V2* r, V2* p, V2* pk,
+                              V2* xk) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double2 v = b[i];
+        V2 c;
+        c.x = v.x;
+        c.y = v.y;
+        V2 z;
+        z.x = 0;
+        z.y = 0;
+        r[i] = c;
+        p[i] = c;
+        for (int k = 0; k < ns; k++) {
+            pk[k * stride + i] = c;
+            xk[k * stride + i] = z;
+        }
+    }
+}
+
+__global__ void k_ms_init_scalars(MSState* st, double tol2, double c_mass) {
+    const double bb = st->bb;
+    st->rr = bb;
+    st->tol2bb = tol2 * bb;
+    st->alpha_old = 1.0;
+    st->beta_old = 0.0;
+    st->iter = 0;
+    st->nonfinite = !isfinite(bb);
+    st->stop_next = 0;
+    int base = 0;
+    for (int k = 1; k < st->n; k++)
+        if (st->shifts[k] < st->shifts[base]) base = k;
+    st->base = base;
+    st->c0 = c_mass + st->shifts[base];
+    for (int k = 0; k < st->n; k++) {
+        st->zeta[k] = st->zeta_old[k] = 1.0;
+        st->active[k] = (bb > 0.0 && isfinite(bb)) ? 1 : 0;
+        st->upd_x[k] = 0;
+        st->iters_shift[k] = 0;
+        st->ak[k] = st->bk[k] = 0.0;
+    }
+    st->n_active = st->active[0] ? st->n : 0;
+    st->live = st->n_active > 0;
+}
+
+// ============================================================== single-shift CG (refinement)
+
+// x_lo += alpha p, r -= alpha w, rr_new = |r|^2; last block: reliable-update test and beta
+template <typename V2, typename R>
+__global__ void k_cg_C(long n, V2* __restrict__ r, const V2* __restrict__ w, const V2* __restrict__ p,
+                       V2* __restrict__ x, CGState* st, double* partials, unsigned int* counter) {
+    if (!st->live) return;
+    const R alpha = (R)st->alpha;
+    double acc = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        V2 rv = r[i], wv = w[i], pv = p[i], xv = x[i];
+        rv.x -= alpha * wv.x;
+        rv.y -= alpha * wv.y;
+        xv.x += alpha * pv.x;
+        xv.y += alpha * pv.y;
+        r[i] = rv;
+        x[i] = xv;
+        acc += (double)(rv.x * rv.x + rv.y * rv.y);
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (last_block(counter)) {
+        double tot = 0.0;
+        for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + i);
+        tot = block_sum(tot);
+        if (threadIdx.x == 0) {
+            st->iter += 1;
+            const int bad = !isfinite(tot);
+            if (bad) st->nonfinite = 1;
+            // reliable update when the residual dropped by delta since the last one,
+            // or when the recursive residual claims convergence
+            const int rel = (tot < st->delta2 * st->rr_max) || (tot <= st->tol2bb);
+            st->want_reliable = rel;
+            st->beta = tot / st->rr;
+            st->rr_prev = st->rr;
+            st->rr = tot;
+            st->stop_next = (rel || bad || st->iter >= st->maxit) ? 1 : 0;
+        }
+    }
+}
+
+// p = r + beta p (skipped when a reliable update is pending: the host does it)
+template <typename V2, typename R>
+__global__ void k_cg_D(long n, const V2* __restrict__ r, V2* __restrict__ p, CGState* st, unsigned int* counter) {
+    if (!st->live) return;
+    if (!st->want_reliable) {
+        const R beta = (R)st->beta;
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+            V2 rv = r[i], pv = p[i];
+            pv.x = rv.x + beta * pv.x;
+            pv.y = rv.y + beta * pv.y;
+            p[i] = pv;
+        }
+    }
+    if (last_block(counter)) {
+        if (threadIdx.x == 0 && st->stop_next) st->live = 0;
+    }
+}
+
+template <typename R, int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_cg_A(Geom g, const void* __restrict__ U,
+                                                  const typename VT<R>::T* __restrict__ p,
+                                                  typename VT<R>::T* __restrict__ t, const CGState* st) {
+    if (!st->live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= g.Vh) return;
+    const Site s = site_of(g, h, 1);
+    Vec3<R> acc = hop2<R, LP>(g, U, p, h, 1, s);
+#pragma unroll
+    for (int a = 0; a < 3; a++) acc.c[a] = (R)0.5 * acc.c[a];
+    st_vec(t, h, acc);
+}
+
+template <typename R, int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_cg_B(Geom g, const void* __restrict__ U,
+                                                  const typename VT<R>::T* __restrict__ t,
+                                                  const typename VT<R>::T* __restrict__ p,
+                                                  typename VT<R>::T* __restrict__ w, CGState* st, double* partials,
+                                                  unsigned int* counter) {
+    if (!st->live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    double pw = mee_second_hop<R, LP>(g, U, t, p, w, (R)st->c0, h);
+    pw = block_sum(pw);
+    if (threadIdx.x == 0) partials[blockIdx.x] = pw;
+    if (last_block(counter)) {
+        double tot = 0.0;
+        for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + i);
+        tot = block_sum(tot);
+        if (threadIdx.x == 0) {
+            st->pw = tot;
+            st->alpha = st->rr / tot;
+        }
+    }
+}
+
+// r = b - w (FP64), |r|^2 -> dst; optionally also the FP32 copy of r
+template <typename V2>
+__global__ void k_residual(long n, const double2* __restrict__ b, const double2* __restrict__ w, double2* r,
+                           V2* rlow, double* partials, unsigned int* counter, double* dst) {
+    double acc = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double2 bv = b[i], wv = w[i];
+        double2 rv = make_double2(bv.x - wv.x, bv.y - wv.y);
+        if (r) r[i] = rv;
+        if (rlow) {
+            V2 c;
+            c.x = rv.x;
+            c.y = rv.y;
+            rlow[i] = c;
+        }
+        acc += rv.x * rv.x + rv.y * rv.y;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (last_block(counter)) finish_sum(partials, gridDim.x, dst);
+}
+
+// x_hi += x_lo (FP64 accumulation of the low-precision correction), x_lo = 0
+template <typename V2>
+__global__ void k_accumulate(long n, double2* xhi, V2* xlo) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        V2 v = xlo[i];
+        double2 x = xhi[i];
+        x.x += (double)v.x;
+        x.y += (double)v.y;
+        xhi[i] = x;
+        v.x = 0;
+        v.y = 0;
+        xlo[i] = v;
+    }
+}
+
+// after a reliable update: p = r + beta p with beta = rr_new / rr_old, and reset scalars
+template <typename V2>
+__global__ void k_cg_restart_p(long n, const V2* __restrict__ r, V2* p, double beta, int reset_p) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        V2 rv = r[i], pv = p[i];
+        if (reset_p) {
+            pv = rv;
+        } else {
+            pv.x = rv.x + (decltype(rv.x))beta * pv.x;
+            pv.y = rv.y + (decltype(rv.x))beta * pv.y;
+        }
+        p[i] = pv;
+    }
+}
+
+// ============================================================== host side
+
+namespace {
+
+struct MSBufs {
+    void *r, *p, *w, *t, *pk, *xk;
+};
+
+template <typename R, int LP>
+void launch_ms_iter(stag_ctx* ctx, const void* U, const MSBufs& b, cudaStream_t s) {
+    typedef typename VT<R>::T V2;
+    const Geom& g = ctx->g;
+    const long n = 3L * g.Vh;
+    const int nb_hop = nblocks(g.Vh, HOP_TPB);
+    const int nb_blas = ctx->num_sms * 4;
+    k_ms_A<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, &ctx->ms->live);
+    k_ms_B<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (V2*)b.w, ctx->ms,
+                                            ctx->partials, ctx->counter);
+    k_ms_C<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (V2*)b.r, (const V2*)b.w, ctx->ms, ctx->partials, ctx->counter);
+    k_ms_D<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, n, (const V2*)b.r, (V2*)b.p, (V2*)b.pk, (V2*)b.xk, ctx->ms,
+                                              ctx->counter);
+}
+
+template <typename R, int LP>
+void launch_cg_iter(stag_ctx* ctx, const void* U, void* r, void* p, void* w, void* t, void* x, cudaStream_t s) {
+    typedef typename VT<R>::T V2;
+    const Geom& g = ctx->g;
+    const long n = 3L * g.Vh;
+    const int nb_hop = nblocks(g.Vh, HOP_TPB);
+    const int nb_blas = ctx->num_sms * 4;
+    k_cg_A<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)p, (V2*)t, ctx->cg);
+    k_cg_B<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)t, (const V2*)p, (V2*)w, ctx->cg, ctx->partials,
+                                            ctx->counter);
+    k_cg_C<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (V2*)r, (const V2*)w, (const V2*)p, (V2*)x, ctx->cg,
+                                              ctx->partials, ctx->counter);
+    k_cg_D<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (const V2*)r, (V2*)p, ctx->cg, ctx->counter);
+}
+
+// Runs `fn` (which enqueues `chunk` iterations) either directly or through a
+// CUDA graph cached under `key`.  The graph is captured on a private stream
+// and launched on `s`.
+template <typename F>
+int run_chunk(stag_ctx* ctx, const std::string& key, int nkernels, F fn, cudaStream_t s) {
+    static int use_graphs = -1;
+    if (use_graphs < 0) use_graphs = env_int("STAG_GRAPHS", 1);
+    ctx->nlaunch += nkernels;
+    if (!use_graphs) {
+        fn(s);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return stag_cuda_check(ctx, e, key.c_str());
+        return STAG_OK;
+    }
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        cudaStream_t cs;
+        STAG_CUDA(ctx, cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        STAG_CUDA(ctx, cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        fn(cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (e != cudaSuccess) return stag_cuda_check(ctx, e, "graph capture");
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return stag_cuda_check(ctx, e, "graph instantiate");
+        it = ctx->graphs.emplace(key, exec).first;
+    }
+    STAG_CUDA(ctx, cudaGraphLaunch(it->second, s));
+    return STAG_OK;
+}
+
+// waits for the stream and copies the state header to the host mirror
+int read_ms_state(stag_ctx* ctx, cudaStream_t s) {
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->ms_host, ctx->ms, sizeof(MSState), cudaMemcpyDeviceToHost, s));
+    STAG_CUDA(ctx, cudaStreamSynchronize(s));
+    return STAG_OK;
+}
+int read_cg_state(stag_ctx* ctx, cudaStream_t s) {
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->cg_host, ctx->cg, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+    STAG_CUDA(ctx, cudaStreamSynchronize(s));
+    return STAG_OK;
+}
+
+// FP64 true residual |b - (M + shift) x|^2 into dscal[slot]; w, t FP64 scratch
+int true_residual2(stag_ctx* ctx, double c, const double2* b, const double2* x, double2* w, double2* t,
+                   double2* r_out, float2* r_low, double* dst, cudaStream_t s) {
+    int st = mee_apply(ctx, STAG_PREC_F64, c, x, w, t, s);
+    if (st) return st;
+    long n = 3L * ctx->g.Vh;
+    k_residual<float2><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n, b, w, r_out, r_low, ctx->partials, ctx->counter,
+                                                             dst);
+    STAG_LAUNCH_CHECK(ctx, "residual");
+    return STAG_OK;
+}
+
+// Shifted CG with vectors of type R and links LP.  b: FP64 source.  On
+// return the FP64 solutions are in xout (n contiguous vectors).
+template <typename R, int LP>
+int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* b, double2* xout,
+            double tol, int maxit, stag_solve_info* info, cudaStream_t s) {
+    typedef typename VT<R>::T V2;
+    const Geom& g = ctx->g;
+    const long n3 = 3L * g.Vh;
+    const size_t vb = sizeof(V2) * n3;
+    const bool f64 = (sizeof(R) == 8);
+    MSBufs bf;
+    bf.r = ws_get(ctx, f64 ? WS_R64 : WS_R32, vb);
+    bf.p = ws_get(ctx, f64 ? WS_P64 : WS_P32, vb);
+    bf.w = ws_get(ctx, f64 ? WS_W64 : WS_W32, vb);
+    bf.t = ws_get(ctx, f64 ? WS_T64 : WS_T32, vb);
+    bf.pk = ws_get(ctx, f64 ? WS_PK64 : WS_PK32, vb * STAG_MAXSHIFT);
+    bf.xk = ws_get(ctx, f64 ? WS_XK64 : WS_XK32, vb * STAG_MAXSHIFT);
+    if (!bf.r || !bf.p || !bf.w || !bf.t || !bf.pk || !bf.xk) return stag_fail(ctx, STAG_ERR_OOM, "solver workspace");
+    if (f64) bf.xk = xout;  // FP64: accumulate straight into the output
+    const void* U = (LP == LP64) ? (const void*)ctx->U64 : (LP == LP32) ? (const void*)ctx->U32 : (const void*)ctx->U16;
+
+    // scalar state
+    MSState* hs = ctx->ms_host;
+    memset(hs, 0, sizeof(MSState));
+    hs->n = n;
+    hs->maxit = maxit;
+    for (int k = 0; k < n; k++) hs->shifts[k] = shifts[k];
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->ms, hs, sizeof(MSState), cudaMemcpyHostToDevice, s));
+    int st = blas_dot_re(ctx, STAG_PREC_F64, b, b, &ctx->ms->bb, s);
+    if (st) return st;
+    k_ms_init_scalars<<<1, 1, 0, s>>>(ctx->ms, tol * tol, mass * mass);
+    k_ms_init_vec<V2><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, n3, n, b, (V2*)bf.r, (V2*)bf.p, (V2*)bf.pk,
+                                                           (V2*)bf.xk);
+    ctx->nlaunch++;
+    STAG_LAUNCH_CHECK(ctx, "ms init");
+
+    const int chunk = env_int("STAG_CHUNK", 16);
+    char key[64];
+    snprintf(key, sizeof key, "ms_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, bf.xk);
+    int guard = 0;
+    for (;;) {
+        st = run_chunk(ctx, key, 4 * chunk, [&](cudaStream_t cs) {
+            for (int i = 0; i < chunk; i++) launch_ms_iter<R, LP>(ctx, U, bf, cs);
+        }, s);
+        if (st) return st;
+        if ((st = read_ms_state(ctx, s))) return st;
+        if (!hs->live) break;
+        if (++guard > maxit / chunk + 4) break;  // cannot happen: the device caps iterations
+    }
+    if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in multi-shift CG");
+    if (info) {
+        info->iters += hs->iter;
+        info->matvecs += hs->iter;
+        for (int k = 0; k < n; k++) info->iters_shift[k] += hs->iters_shift[k];
+    }
+    if (!f64) {
+        if ((st = blas_copy_f2d(ctx, (const float2*)bf.xk, xout, (long)g.Vh * n, s))) return st;
+    }
+    return STAG_OK;
+}
+
+// Mixed-precision CG with FP64 reliable updates for (M + shift) x = b,
+// starting from the FP64 guess x (updated in place).  Returns the FP64 true
+// residual^2 in *rr_true.
+template <int LP>
+int refine_shift(stag_ctx* ctx, double mass, double shift, const double2* b, double bb, double2* x, double tol,
+                 int maxit, double* rr_true, int* iters, int* reliable, int* matvecs, cudaStream_t s) {
+    const Geom& g = ctx->g;
+    const long n3 = 3L * g.Vh;
+    const size_t vb32 = sizeof(float2) * n3, vb64 = sizeof(double2) * n3;
+    float2* r32 = (float2*)ws_get(ctx, WS_R32, vb32);
+    float2* p32 = (float2*)ws_get(ctx, WS_P32, vb32);
+    float2* w32 = (float2*)ws_get(ctx, WS_W32, vb32);
+    float2* t32 = (float2*)ws_get(ctx, WS_T32, vb32);
+    float2* x32 = (float2*)ws_get(ctx, WS_XLO, vb32);
+    double2* w64 = (double2*)ws_get(ctx, WS_W64, vb64);
+    double2* t64 = (double2*)ws_get(ctx, WS_T64, vb64);
+    if (!r32 || !p32 || !w32 || !t32 || !x32 || !w64 || !t64) return stag_fail(ctx, STAG_ERR_OOM, "refine workspace");
+    const void* U = (LP == LP32) ? (const void*)ctx->U32 : (const void*)ctx->U16;
+    const double c = mass * mass + shift;
+    const double delta = env_dbl("STAG_RELIABLE_DELTA", 0.1);
+    const int chunk = env_int("STAG_CHUNK", 16);
+    int st;
+
+    double* dres = ctx->dscal + 0;
+    if ((st = true_residual2(ctx, c, b, x, w64, t64, nullptr, r32, dres, s))) return st;
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal, dres, sizeof(double), cudaMemcpyDeviceToHost, s));
+    STAG_CUDA(ctx, cudaStreamSynchronize(s));
+    double rr = ctx->hscal[0];
+    *matvecs += 1;
+    const double tol2bb = tol * tol * bb;
+    if (rr <= tol2bb) {
+        *rr_true = rr;
+        return STAG_OK;
+    }
+    STAG_CUDA(ctx, cudaMemsetAsync(x32, 0, vb32, s));
+    k_cg_restart_p<float2><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, r32, p32, 0.0, 1);
+    STAG_LAUNCH_CHECK(ctx, "cg start");
+    CGState* hs = ctx->cg_host;
+    memset(hs, 0, sizeof(CGState));
+    hs->rr = rr;
+    hs->rr_max = rr;
+    hs->bb = bb;
+    hs->tol2bb = tol2bb;
+    hs->delta2 = delta * delta;
+    hs->c0 = c;
+    hs->maxit = maxit;
+    hs->live = 1;
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->cg, hs, sizeof(CGState), cudaMemcpyHostToDevice, s));
+    char key[64];
+    snprintf(key, sizeof key, "cg_%d_%d", LP, chunk);
+    int total_iter = 0;
+    for (;;) {
+        st = run_chunk(ctx, key, 4 * chunk, [&](cudaStream_t cs) {
+            for (int i = 0; i < chunk; i++) launch_cg_iter<float, LP>(ctx, U, r32, p32, w32, t32, x32, cs);
+        }, s);
+        if (st) return st;
+        if ((st = read_cg_state(ctx, s))) return st;
+        if (hs->live) continue;
+        total_iter = hs->iter;
+        if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in CG");
+        // reliable update: x += x_lo in FP64, true residual in FP64
+        k_accumulate<float2><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, x, x32);
+        STAG_LAUNCH_CHECK(ctx, "accumulate");
+        if ((st = true_residual2(ctx, c, b, x, w64, t64, nullptr, r32, dres, s))) return st;
+        STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal, dres, sizeof(double), cudaMemcpyDeviceToHost, s));
+        STAG_CUDA(ctx, cudaStreamSynchronize(s));
+        *matvecs += 1;
+        *reliable += 1;
+        const double rr_t = ctx->hscal[0];
+        if (rr_t <= tol2bb || hs->iter >= maxit) {
+            *rr_true = rr_t;
+            break;
+        }
+        // continue the recursion on the true residual, keeping the search
+        // direction: p = r_true + (|r_true|^2 / |r_prev|^2) p
+        const double beta = rr_t / hs->rr_prev;
+        k_cg_restart_p<float2><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, r32, p32, beta, 0);
+        STAG_LAUNCH_CHECK(ctx, "cg restart");
+        hs->rr = rr_t;
+        hs->rr_max = rr_t;
+        hs->live = 1;
+        hs->stop_next = 0;
+        hs->want_reliable = 0;
+        STAG_CUDA(ctx, cudaMemcpyAsync(ctx->cg, hs, sizeof(CGState), cudaMemcpyHostToDevice, s));
+    }
+    *iters += total_iter;
+    *matvecs += total_iter;
+    return STAG_OK;
+}
+
+}  // namespace
+
+int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src,
+                     double2* const* sols, double tol, int maxit, int mode, stag_solve_info* info, cudaStream_t s) {
+    if (n < 1 || n > STAG_MAXSHIFT) return stag_fail(ctx, STAG_ERR_ARG, "number of shifts %d out of range", n);
+    for (int k = 0; k < n; k++)
+        if (!(shifts[k] >= 0.0)) return stag_fail(ctx, STAG_ERR_ARG, "shift %d negative or NaN", k);
+    if (!(tol > 0.0) || maxit < 1) return stag_fail(ctx, STAG_ERR_ARG, "bad tolerance or iteration cap");
+    const Geom& g = ctx->g;
+    const long n3 = 3L * g.Vh;
+    const size_t vb64 = sizeof(double2) * n3;
+    stag_solve_info local;
+    if (!info) info = &local;
+    memset(info, 0, sizeof(*info));
+
+    // contiguous FP64 solutions: the caller's buffers are filled at the end
+    double2* X = (double2*)ws_get(ctx, WS_FX, vb64 * STAG_MAXSHIFT);
+    if (!X) return stag_fail(ctx, STAG_ERR_OOM, "solution workspace");
+    int st;
+    if (mode == STAG_SOLVE_F64) {
+        st = ms_core<double, LP64>(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
+    } else if (mode == STAG_SOLVE_MIXED || mode == STAG_SOLVE_MIXED_BF16) {
+        const double tol_ms = fmax(tol, env_dbl("STAG_MS_TOL32", 1e-6));
+        if (mode == STAG_SOLVE_MIXED)
+            st = ms_core<float, LP32>(ctx, mass, n, shifts, src, X, tol_ms, maxit, info, s);
+        else
+            st = ms_core<float, LP16>(ctx, mass, n, shifts, src, X, tol_ms, maxit, info, s);
+    } else {
+        return stag_fail(ctx, STAG_ERR_ARG, "unknown solver mode %d", mode);
+    }
+    if (st) return st;
+
+    // FP64 true residual of every shift; mixed mode refines the ones above tol
+    double2* w64 = (double2*)ws_get(ctx, WS_W64, vb64);
+    double2* t64 = (double2*)ws_get(ctx, WS_T64, vb64);
+    if ((st = blas_dot_re(ctx, STAG_PREC_F64, src, src, ctx->dscal + 1, s))) return st;
+    for (int k = 0; k < n; k++) {
+        if ((st = true_residual2(ctx, mass * mass + shifts[k], src, X + k * n3, w64, t64, nullptr, nullptr,
+                                 ctx->dscal + 100 + k, s)))
+            return st;
+    }
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * (100 + n), cudaMemcpyDeviceToHost, s));
+    STAG_CUDA(ctx, cudaStreamSynchronize(s));
+    info->matvecs += n;
+    const double bb = ctx->hscal[1];
+    double rr[STAG_MAXSHIFT];
+    for (int k = 0; k < n; k++) rr[k] = ctx->hscal[100 + k];
+    int status = STAG_OK;
+    for (int k = 0; k < n; k++) {
+        if (bb == 0.0) {
+            info->true_resid[k] = 0.0;
+            continue;
+        }
+        if (mode != STAG_SOLVE_F64 && rr[k] > tol * tol * bb) {
+            int it = 0, rel = 0, mv = 0;
+            double rrt = rr[k];
+            if (mode == STAG_SOLVE_MIXED)
+                st = refine_shift<LP32>(ctx, mass, shifts[k], src, bb, X + k * n3, tol, maxit, &rrt, &it, &rel, &mv, s);
+            else
+                st = refine_shift<LP16>(ctx, mass, shifts[k], src, bb, X + k * n3, tol, maxit, &rrt, &it, &rel, &mv, s);
+            if (st) return st;
+            rr[k] = rrt;
+            info->refine_iters[k] = it;
+            info->reliable_updates += rel;
+            info->matvecs += mv;
+        }
+        info->true_resid[k] = sqrt(rr[k] / bb);
+        if (!isfinite(info->true_resid[k])) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite solution");
+        if (rr[k] > tol * tol * bb * 1.0000001) status = STAG_ERR_NOCONV;
+    }
+    if (sols) {
+        for (int k = 0; k < n; k++)
+            if (sols[k] && sols[k] != X + k * n3)
+                STAG_CUDA(ctx, cudaMemcpyAsync(sols[k], X + k * n3, vb64, cudaMemcpyDeviceToDevice, s));
+    }
+    info->status = status;
+    if (status) return stag_fail(ctx, status, "solver did not reach tolerance %.3g", tol);
+    return STAG_OK;
+}

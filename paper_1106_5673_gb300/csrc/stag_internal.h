@@ -1,0 +1,136 @@
+// stag_internal.h -- context object and cross-file declarations of the
+// GB300 staggered-RHMC library.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/stag.h"
+#include "lattice.cuh"
+
+#define STAG_RED_MAXBLOCKS 8192  // max blocks of any reducing kernel
+#define STAG_NSCAL 256           // doubles in the device scalar area
+
+// Work buffers, allocated on first use and grown on demand.
+enum WsSlot {
+    WS_STAGE = 0,   // canonical <-> internal conversion staging
+    WS_R64, WS_P64, WS_W64, WS_T64,       // FP64 solver vectors (T: odd-parity temp)
+    WS_PK64, WS_XK64,                     // FP64 shifted p_k / x_k, n vectors each
+    WS_R32, WS_P32, WS_W32, WS_T32,       // FP32 solver vectors
+    WS_PK32, WS_XK32,                     // FP32 shifted p_k / x_k
+    WS_XHI, WS_RHI, WS_B64,               // refinement (FP64 solution, residual, rhs)
+    WS_XLO,                               // refinement FP32 correction
+    WS_FX, WS_FY,                         // force: X_k (even), Y_k (odd), FP64
+    WS_PHI, WS_RGAUSS, WS_RAT,            // trajectory: pseudofermions, R, r(M) phi
+    WS_FORCE,                             // force accumulator [4][2][8][Vh] doubles
+    WS_NSLOTS
+};
+
+// Device-resident scalar state of one multi-shift CG (Eq. (13)).
+struct MSState {
+    double rr, bb, alpha, alpha_old, beta, beta_old, pw, tol2bb, c0;
+    double zeta[STAG_MAXSHIFT], zeta_old[STAG_MAXSHIFT], zeta_next[STAG_MAXSHIFT];
+    double ak[STAG_MAXSHIFT], bk[STAG_MAXSHIFT], shifts[STAG_MAXSHIFT];
+    int upd_x[STAG_MAXSHIFT], active[STAG_MAXSHIFT], iters_shift[STAG_MAXSHIFT];
+    int n, base, iter, maxit;
+    int live;       // 1 while iterating
+    int stop_next;  // set by the residual update, applied by the last kernel of the iteration
+    int n_active;
+    int nonfinite;
+};
+
+// Device-resident scalar state of one single-shift CG with reliable updates.
+struct CGState {
+    double rr, rr_prev, rr_max, alpha, beta, pw, bb, tol2bb, delta2, c0;
+    int iter, maxit, live, stop_next, want_reliable, nonfinite;
+};
+
+struct stag_ctx {
+    Geom g;
+    int device;
+    char err[512];
+    double2* U64;       // [4][2][6][Vh]
+    float4* U32;        // [4][2][3][Vh]
+    uint2* U16;         // [4][2][3][Vh]
+    double2* U64_save;  // copy kept for the Metropolis reject
+    double* mom;        // [4][2][8][Vh]
+    int gauge_loaded;
+    double* partials;   // reduction partials
+    unsigned int* counter;
+    double* dscal;      // device scalar area (STAG_NSCAL doubles)
+    double* hscal;      // pinned host mirror of dscal
+    MSState* ms;        // device multi-shift state
+    MSState* ms_host;   // pinned host mirror
+    CGState* cg;        // device single-shift state
+    CGState* cg_host;   // pinned host mirror
+    void* ws[WS_NSLOTS];
+    size_t ws_bytes[WS_NSLOTS];
+    size_t fixed_bytes;
+    std::map<std::string, cudaGraphExec_t> graphs;
+    int num_sms;
+    long long nlaunch;  // kernels launched (graph nodes counted individually)
+};
+
+// ---------------------------------------------------------------- utilities (capi.cu)
+int stag_fail(stag_ctx* ctx, int code, const char* fmt, ...);
+int stag_cuda_check(stag_ctx* ctx, cudaError_t e, const char* what);
+void* ws_get(stag_ctx* ctx, int slot, size_t bytes);
+#define STAG_CUDA(ctx, call)                                              \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return stag_cuda_check(ctx, e_, #call);    \
+    } while (0)
+#define STAG_LAUNCH_CHECK(ctx, what)                                      \
+    do {                                                                  \
+        (ctx)->nlaunch++;                                                 \
+        cudaError_t e_ = cudaGetLastError();                              \
+        if (e_ != cudaSuccess) return stag_cuda_check(ctx, e_, what);     \
+    } while (0)
+
+static inline int nblocks(long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+// ---------------------------------------------------------------- gauge.cu
+int gauge_from_canonical(stag_ctx* ctx, const double* dev_links, cudaStream_t s);
+int gauge_to_canonical(stag_ctx* ctx, double* dev_links, cudaStream_t s);
+int momenta_from_canonical(stag_ctx* ctx, const double* dev_w, cudaStream_t s);
+int momenta_to_canonical(stag_ctx* ctx, const double* src_internal, double* dev_w, cudaStream_t s);
+int plaquette_sum(stag_ctx* ctx, double* dst_dev, cudaStream_t s);         // sum Re Tr U_P / 3
+int kinetic_sum(stag_ctx* ctx, double* dst_dev, cudaStream_t s);           // 1/2 sum w^2
+// F (internal layout) = coeff * gauge force (+ F if accumulate)
+int gauge_force_internal(stag_ctx* ctx, double beta, double* F, int accumulate, cudaStream_t s);
+int update_links(stag_ctx* ctx, double eps, cudaStream_t s);
+int update_momenta(stag_ctx* ctx, const double* F, double eps, cudaStream_t s);
+int momenta_heatbath(stag_ctx* ctx, uint32_t seed, uint32_t traj, cudaStream_t s);
+int pf_gaussian(stag_ctx* ctx, uint32_t seed, uint32_t traj, int pf, double2* out, cudaStream_t s);
+int metro_uniform(stag_ctx* ctx, uint32_t seed, uint32_t traj, double* dst_dev, cudaStream_t s);
+
+// ---------------------------------------------------------------- dslash.cu
+// out = 1/2 hop (plain D restricted to out_par)
+int dslash_apply(stag_ctx* ctx, int prec, const void* in, void* out, int out_par, cudaStream_t s);
+// out = c * in - D_eo D_oe in, with tmp (odd) scratch
+int mee_apply(stag_ctx* ctx, int prec, double c, const void* in, void* out, void* tmp, cudaStream_t s);
+// multi-RHS: out[k] = D_oe in[k] for nrhs FP64 vectors (contiguous, stride Vh*3)
+int dslash_multi64(stag_ctx* ctx, const double2* in, double2* out, int nrhs, int out_par, cudaStream_t s);
+
+// ---------------------------------------------------------------- blas.cu
+int blas_dot_re(stag_ctx* ctx, int prec, const void* a, const void* b, double* dst_dev, cudaStream_t s);
+int blas_copy_d2f(stag_ctx* ctx, const double2* in, float2* out, long nvec_sites, cudaStream_t s);
+int blas_copy_f2d(stag_ctx* ctx, const float2* in, double2* out, long nvec_sites, cudaStream_t s);
+// out = a0 * src + sum_k a_k x_k (FP64)
+int blas_rational_combine(stag_ctx* ctx, double a0, const double* a, int n, const double2* src,
+                          const double2* x, double2* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- solver.cu
+int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src,
+                     double2* const* sols, double tol, int maxit, int mode, stag_solve_info* info,
+                     cudaStream_t s);
+
+// ---------------------------------------------------------------- force.cu
+// F (internal) (+)= fermion force for sum_k a_k X_k, Y_k = D_oe X_k; X contiguous FP64
+int fermion_force_assemble(stag_ctx* ctx, const stag_rational* r, const double2* X, double* F,
+                           int accumulate, cudaStream_t s);

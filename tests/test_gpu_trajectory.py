@@ -1,0 +1,91 @@
+"""GPU parity of whole RHMC trajectories against the FP64 oracle.
+
+The 4^4 workload: Wilson beta = 5.3, m = 0.1, links exp(i 0.3 H) (seed 0),
+degree-8 rationals on [1e-3, 64], solver tolerance 1e-10, leapfrog tau = 1
+with 10 steps.  FP64 mode must give the oracle's dH to 1e-8 absolute (the
+solves stop at 1e-10 relative, both sides in FP64) and the same
+accept/reject decision; mixed mode the same decision and dH to 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1106_5673_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1106_5673_gb300 import build, stag
+    build.build()
+    return stag
+
+
+def _rats(rationals, key):
+    h = rationals["p+1/4_" + key]
+    r = rationals["p-1/2_" + key]
+    return (h["a0"], h["a"], h["b"]), (r["a0"], r["a"], r["b"])
+
+
+def _run_both(S, rationals, dims, integrator, nsteps, tau, mode, seed_links=0, traj=0, beta=5.3,
+              mass=0.1, key="d8_1e-3"):
+    hb, act = _rats(rationals, key)
+    U = synth.near_unit_links(dims, 0.3, seed_links)
+    po = O.make_params(beta, mass, tau, nsteps, integrator, hb, act, act, tol_md=1e-10,
+                       tol_metro=1e-10, seed=11, traj=traj)
+    Uo, io, st = O.trajectory(dims, U, po)
+    assert st == 0
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    pg = S.make_params(beta, mass, tau, nsteps, integrator, hb, act, act, tol_md=1e-10,
+                       tol_metro=1e-10, mode_md=mode, mode_metro=mode, seed=11, traj=traj)
+    ig = L.md_trajectory(pg)
+    return U, Uo, io, L.store_gauge(), ig
+
+
+def test_trajectory_4x4x4x4_leapfrog_f64(S, rationals):
+    U, Uo, io, Ug, ig = _run_both(S, rationals, (4, 4, 4, 4), 0, 10, 1.0, S.SOLVE_F64)
+    assert ig["n_force"] == io["n_force"] == 11
+    assert abs(ig["u"] - io["u"]) < 1e-15
+    assert abs(ig["H0"] - io["H0"]) < 1e-8 * abs(io["H0"])
+    assert abs(ig["dH"] - io["dH"]) < 1e-8
+    assert ig["accepted"] == io["accepted"]
+    assert np.abs(Ug - Uo).max() < 1e-9
+    assert abs(ig["plaq"] - io["plaq"]) < 1e-12
+
+
+def test_trajectory_4x4x4x4_leapfrog_mixed(S, rationals):
+    U, Uo, io, Ug, ig = _run_both(S, rationals, (4, 4, 4, 4), 0, 10, 1.0, S.SOLVE_MIXED)
+    assert abs(ig["dH"] - io["dH"]) < 1e-6 * max(1.0, abs(io["dH"]))
+    assert ig["accepted"] == io["accepted"]
+    assert np.abs(Ug - Uo).max() < 1e-6
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_trajectory_omelyan_rectangular(S, rationals, mode):
+    """Omelyan 2MN on a 6x4x6x10 lattice (ragged last block), degree 6."""
+    U, Uo, io, Ug, ig = _run_both(S, rationals, (6, 4, 6, 10), 1, 4, 0.5, mode, seed_links=3,
+                                  traj=5, key="d6_1e-2", mass=0.2)
+    assert ig["n_force"] == io["n_force"] == 9
+    # mixed mode integrates with FP32 forces: the trajectory moves by ~1e-7
+    # relative, so dH agrees to 1e-6 relative to max(1, |dH|)
+    tol = 1e-8 if mode == 0 else 1e-6 * max(1.0, abs(io["dH"]))
+    assert abs(ig["dH"] - io["dH"]) < tol
+    assert ig["accepted"] == io["accepted"]
+
+
+def test_trajectory_rejection_restores_links(S, rationals):
+    """A far too coarse integrator (1 step, tau = 2) is rejected: links restored."""
+    dims = (4, 4, 4, 4)
+    hb, act = _rats(rationals, "d8_1e-3")
+    U = synth.near_unit_links(dims, 0.3, 0)
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    p = S.make_params(5.3, 0.1, 2.0, 1, 0, hb, act, act, seed=3, traj=1)
+    info = L.md_trajectory(p)
+    assert info["dH"] > 5 and not info["accepted"]
+    np.testing.assert_allclose(L.store_gauge(), U, atol=2e-15)
