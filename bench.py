@@ -195,6 +195,7 @@ def reference_arm(args):
 
 
 def main():
+    global NSTEPS, ROOF_DIMS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -203,9 +204,29 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--ref-iters", type=int, default=50000)
+    ap.add_argument("--mode", default="mixed", choices=["mixed", "f64", "ff", "bf16"],
+                    help="solver mode of the timed trajectories")
+    ap.add_argument("--nsteps", type=int, default=NSTEPS,
+                    help="MD steps (profiling runs only; the workload is 20)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e and roofline measurements (profiling runs)")
+    ap.add_argument("--roofline-only", action="store_true",
+                    help="only time the FP32 hop on the roofline lattice")
+    ap.add_argument("--roof-dims", default="64,64,64,16",
+                    help="lattice of the large-lattice hop roofline, e.g. 48,48,48,16")
     args = ap.parse_args()
+    ROOF_DIMS = tuple(int(x) for x in args.roof_dims.split(","))
     if args.impl == "reference":
         return reference_arm(args)
+    NSTEPS = args.nsteps
+    if args.roofline_only:
+        import torch
+        from paper_1106_5673_gb300 import stag
+        r = hop_roofline(stag, torch, ROOF_DIMS)
+        peak, kind = _peaks()
+        print(json.dumps({"roofline_only": r, "frac": r["gbs"] / peak, "peak": peak,
+                          "peak_kind": kind}))
+        return 0
 
     import torch
     import torch.distributed as dist
@@ -229,9 +250,13 @@ def main():
     L = stag.Lattice(DIMS)
     L.load_gauge(U0)
 
-    # warm-up trajectories (untimed), then K timed ones: mixed precision
+    MODES = {"mixed": stag.SOLVE_MIXED, "f64": stag.SOLVE_F64, "ff": stag.SOLVE_F64FF,
+             "bf16": stag.SOLVE_MIXED_BF16}
+    mode = MODES[args.mode]
+
+    # warm-up trajectories (untimed), then K timed ones
     for i in range(args.warmup):
-        L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED, i, 100 + rank))
+        L.md_trajectory(_params(stag, rat_hb, rat_act, mode, i, 100 + rank))
     n0 = L.launch_count()
     clocks = ClockSampler(_gpu_uuid(torch, local))
     barrier()
@@ -241,8 +266,8 @@ def main():
     e0.record()
     infos = []
     for k in range(args.steps):
-        infos.append(L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED,
-                                             args.warmup + k, 100 + rank)))
+        infos.append(L.md_trajectory(_params(stag, rat_hb, rat_act, mode, args.warmup + k,
+                                             100 + rank)))
     e1.record()
     torch.cuda.synchronize()
     barrier()
@@ -254,38 +279,41 @@ def main():
         t = float(tt.item())
     launches = L.launch_count() - n0
     value = t / (args.steps * world)
-    iters_mixed = sum(i["cg_iters"] for i in infos) / len(infos)
+    iters_timed = sum(i["cg_iters"] for i in infos) / len(infos)
 
-    # plain FP64 GPU form of the same trajectory (same start, same random numbers)
-    fp64 = None
+    # the plain FP64 GPU form and the float-float form of the next trajectory,
+    # from the same start with the same random numbers, beside the timed mode
+    compare = None
     if not args.no_fp64:
-        L2 = stag.Lattice(DIMS)
-        L2.load_gauge(L.store_gauge())
+        Ustart = L.store_gauge()
         traj = args.warmup + args.steps
+        compare = {}
+        for name, m in (("f64", stag.SOLVE_F64), ("ff", stag.SOLVE_F64FF), (args.mode, mode)):
+            L2 = stag.Lattice(DIMS)
+            L2.load_gauge(Ustart)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            i2 = L2.md_trajectory(_params(stag, rat_hb, rat_act, m, traj, 100 + rank))
+            torch.cuda.synchronize()
+            compare[name] = {"s_per_traj": time.perf_counter() - t0, "cg_iters": i2["cg_iters"],
+                             "dH": i2["dH"], "accepted": i2["accepted"]}
+            L2.close()
+        compare["speedup_vs_f64"] = compare["f64"]["s_per_traj"] / value if world == 1 else None
+
+    t_e2e, roof, roof_large = None, None, None
+    link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
+    if not args.no_extras:
+        # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
+        Uh = L.store_gauge()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        i64 = L2.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_F64, traj, 100 + rank))
-        t64 = time.perf_counter() - t0
-        im = L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED, traj, 100 + rank))
-        fp64 = {"s_per_traj": t64, "cg_iters": i64["cg_iters"], "dH": i64["dH"],
-                "accepted": i64["accepted"], "mixed_dH_same_start": im["dH"],
-                "mixed_accepted_same_start": im["accepted"], "speedup_mixed": t64 / value
-                if world == 1 else None}
-        L2.close()
-
-    # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
-    Uh = L.store_gauge()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    L.load_gauge(Uh)
-    L.md_trajectory(_params(stag, rat_hb, rat_act, stag.SOLVE_MIXED, 999, 100 + rank))
-    Uh = L.store_gauge()
-    torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
-
-    roof = hop_roofline(stag, torch, DIMS)
-    roof_large = hop_roofline(stag, torch, ROOF_DIMS)
+        L.load_gauge(Uh)
+        L.md_trajectory(_params(stag, rat_hb, rat_act, mode, 999, 100 + rank))
+        Uh = L.store_gauge()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        roof = hop_roofline(stag, torch, DIMS)
+        roof_large = hop_roofline(stag, torch, ROOF_DIMS)
     peak, peak_kind = _peaks()
 
     line = {
@@ -299,24 +327,28 @@ def main():
                    "solver": "mixed: fp32 multishift + fp64 reliable-update refinement",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "working set > L2 (links fp64+fp32+bf16 ~176 MB, solver vectors ~200 MB)"},
-        "roofline": {"bound": "hbm", "achieved": roof["gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": roof["gbs"] / peak, "traffic": None,
-                     "kernel": "k_hop<float,LP32> (D_oe, FP32 12-real links)",
-                     "dims": roof["dims"], "peak_kind": peak_kind},
-        "roofline_large": {"bound": "hbm", "achieved": roof_large["gbs"], "peak": peak,
-                           "unit": "GB/s", "frac": roof_large["gbs"] / peak,
-                           "dims": roof_large["dims"], "gflops": roof_large["gflops"]},
-        "e2e": {"value": t_e2e, "unit": "s/trajectory", "h2d_bytes_per_step": link_bytes,
-                "d2h_bytes_per_step": link_bytes},
+        "roofline": None if roof is None else {
+            "bound": "hbm", "achieved": roof["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": roof["gbs"] / peak, "traffic": None,
+            "kernel": "k_hop<float,LP32> (D_oe, FP32 12-real links)",
+            "dims": roof["dims"], "peak_kind": peak_kind},
+        "roofline_large": None if roof_large is None else {
+            "bound": "hbm", "achieved": roof_large["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": roof_large["gbs"] / peak, "dims": roof_large["dims"],
+            "gflops": roof_large["gflops"]},
+        "e2e": None if t_e2e is None else {
+            "value": t_e2e, "unit": "s/trajectory", "h2d_bytes_per_step": link_bytes,
+            "d2h_bytes_per_step": link_bytes},
         "gpu_launches": launches,
         "clocks": ck,
         "trajectories": [{k: i[k] for k in ("dH", "accepted", "plaq", "cg_iters", "n_force",
                                              "t_md", "t_total")} for i in infos],
-        "cg_iters_per_traj_mixed": iters_mixed,
-        "fp64_compare": fp64,
+        "mode": args.mode,
+        "cg_iters_per_traj": iters_timed,
+        "compare_same_start": compare,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        iters = fp64["cg_iters"] if fp64 else (REF_ITERS_PER_TRAJ or args.ref_iters)
+        iters = compare["f64"]["cg_iters"] if compare else (REF_ITERS_PER_TRAJ or args.ref_iters)
         line["cpu_baseline"] = cpu_sample(U0, rat_act, iters, infos[0]["n_force"])
     if rank == 0:
         print(json.dumps(line))

@@ -54,11 +54,21 @@ enum {
     STAG_ERR_STATE = -6      /* call out of order (e.g. no gauge field loaded)         */
 };
 
-enum { STAG_PREC_F64 = 0, STAG_PREC_F32 = 1, STAG_PREC_BF16 = 2 };
+/* Operator precisions.  F64FF takes and returns FP64 vectors but computes in
+ * float-float arithmetic on the FP32 units (each double carried as a pair of
+ * floats hi + lo, Sec. 4.2's split used for arithmetic): relative accuracy
+ * ~1e-13, many times the throughput of GB300's FP64 units. */
+enum { STAG_PREC_F64 = 0, STAG_PREC_F32 = 1, STAG_PREC_BF16 = 2, STAG_PREC_F64FF = 3 };
 
-/* Solver modes: plain FP64, or FP32/BF16 bulk with FP64 reliable updates and
- * an FP64 true-residual check of every shift. */
-enum { STAG_SOLVE_F64 = 0, STAG_SOLVE_MIXED = 1, STAG_SOLVE_MIXED_BF16 = 2 };
+/* Solver modes:
+ *  F64         plain FP64 shifted CG, FP64 true-residual check of every shift;
+ *  MIXED       FP32 shifted CG, then the shifts above tolerance refined
+ *              together by a batched CG (multi-RHS hops, FP32 recursion, FP64
+ *              reliable updates); every shift checked FP64-accurately;
+ *  MIXED_BF16  as MIXED with BF16 links in the FP32 kernels;
+ *  F64FF       FP64 vectors and recurrences with the float-float operator
+ *              (STAG_PREC_F64FF) in place of native FP64 arithmetic. */
+enum { STAG_SOLVE_F64 = 0, STAG_SOLVE_MIXED = 1, STAG_SOLVE_MIXED_BF16 = 2, STAG_SOLVE_F64FF = 3 };
 
 enum { STAG_INT_LEAPFROG = 0, STAG_INT_OMELYAN = 1 };
 
@@ -147,7 +157,8 @@ int stag_gauge_action(stag_ctx *ctx, double beta, double *action, void *stream);
 
 /* out_even = D_eo in_odd:  (D psi)(n) = 1/2 sum_mu eta_mu(n) [U_mu(n) psi(n+mu)
  * - U_mu(n-mu)^dag psi(n-mu)].  Device vectors in the canonical layout of
- * `prec` (F64: complex128; F32, BF16: complex64, with FP32 resp. BF16 links). */
+ * `prec` (F64, F64FF: complex128; F32, BF16: complex64, with FP32 resp. BF16
+ * links).  in and out must not alias. */
 int stag_apply_deo(stag_ctx *ctx, const void *in_odd, void *out_even, int prec, void *stream);
 /* out_odd = D_oe in_even. */
 int stag_apply_doe(stag_ctx *ctx, const void *in_even, void *out_odd, int prec, void *stream);

@@ -96,12 +96,13 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const size_t Vh = ctx->g.Vh;
-    int maxb = (int)(Vh / 64 + 2);
+    int maxb = (int)(4 * (Vh / 128 + 2));  // four partial sums per hop block
     if (maxb < (int)(V / 256 + 2)) maxb = (int)(V / 256 + 2);
     if (maxb < 16 * ctx->num_sms) maxb = 16 * ctx->num_sms;
     struct { void** p; size_t bytes; } allocs[] = {
         {(void**)&ctx->U64, sizeof(double2) * 48 * Vh},
         {(void**)&ctx->U32, sizeof(float4) * 24 * Vh},
+        {(void**)&ctx->U32lo, sizeof(float4) * 24 * Vh},
         {(void**)&ctx->U16, sizeof(uint2) * 24 * Vh},
         {(void**)&ctx->U64_save, sizeof(double2) * 48 * Vh},
         {(void**)&ctx->mom, sizeof(double) * 64 * Vh},
@@ -110,6 +111,7 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
         {(void**)&ctx->dscal, sizeof(double) * STAG_NSCAL},
         {(void**)&ctx->ms, sizeof(MSState)},
         {(void**)&ctx->cg, sizeof(CGState)},
+        {(void**)&ctx->bcg, sizeof(BCGState)},
     };
     ctx->fixed_bytes = 0;
     for (auto& a : allocs) {
@@ -122,6 +124,7 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->hscal, sizeof(double) * STAG_NSCAL);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->ms_host, sizeof(MSState));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->cg_host, sizeof(CGState));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->bcg_host, sizeof(BCGState));
     if (e != cudaSuccess) {
         st = (e == cudaErrorMemoryAllocation) ? STAG_ERR_OOM : STAG_ERR_CUDA;
         cudaGetLastError();
@@ -136,8 +139,8 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     if (!ctx) return STAG_OK;
     cudaDeviceSynchronize();
     clear_graphs(ctx);
-    void* ps[] = {ctx->U64, ctx->U32, ctx->U16, ctx->U64_save, ctx->mom, ctx->partials,
-                  ctx->counter, ctx->dscal, ctx->ms, ctx->cg};
+    void* ps[] = {ctx->U64, ctx->U32, ctx->U32lo, ctx->U16, ctx->U64_save, ctx->mom, ctx->partials,
+                  ctx->counter, ctx->dscal, ctx->ms, ctx->cg, ctx->bcg};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int i = 0; i < WS_NSLOTS; i++)
@@ -145,6 +148,7 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     if (ctx->hscal) cudaFreeHost(ctx->hscal);
     if (ctx->ms_host) cudaFreeHost(ctx->ms_host);
     if (ctx->cg_host) cudaFreeHost(ctx->cg_host);
+    if (ctx->bcg_host) cudaFreeHost(ctx->bcg_host);
     delete ctx;
     return STAG_OK;
 }
@@ -286,9 +290,10 @@ int stag_apply_M(stag_ctx* ctx, double mass, const void* in_even, void* out_even
     CHECK_PTR(ctx, in_even);
     CHECK_PTR(ctx, out_even);
     if (in_even == out_even) return stag_fail(ctx, STAG_ERR_ARG, "in and out alias");
-    if (prec < 0 || prec > 2) return stag_fail(ctx, STAG_ERR_ARG, "unknown precision %d", prec);
-    const size_t vb = (prec == STAG_PREC_F64 ? sizeof(double2) : sizeof(float2)) * 3 * (size_t)ctx->g.Vh;
-    void* tmp = ws_get(ctx, prec == STAG_PREC_F64 ? WS_RHI : WS_XK32, vb);
+    if (prec < 0 || prec > 3) return stag_fail(ctx, STAG_ERR_ARG, "unknown precision %d", prec);
+    const int dbl = (prec == STAG_PREC_F64 || prec == STAG_PREC_F64FF);
+    const size_t vb = (dbl ? sizeof(double2) : sizeof(float2)) * 3 * (size_t)ctx->g.Vh;
+    void* tmp = ws_get(ctx, dbl ? WS_RHI : WS_XLO, vb);
     if (!tmp) return stag_fail(ctx, STAG_ERR_OOM, "temporary");
     return mee_apply(ctx, prec, mass * mass, in_even, out_even, tmp, S(stream));
 }

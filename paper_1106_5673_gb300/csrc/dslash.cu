@@ -38,9 +38,34 @@ static void launch_hop(stag_ctx* ctx, const void* U, const void* in, void* out, 
         (const typename VT<R>::T*)self);
 }
 
+// FP64-accurate hop in float-float arithmetic (FP64 vectors in and out)
+__global__ void __launch_bounds__(HOP_TPB) k_hop_ff(Geom g, const float4* __restrict__ Uhi,
+                                                    const float4* __restrict__ Ulo, const double2* __restrict__ in,
+                                                    double2* __restrict__ out, int par, double scale, double c,
+                                                    const double2* __restrict__ self) {
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= g.Vh) return;
+    const Site s = site_of(g, h, par);
+    Vec3<double> acc = hop2_ff(g, Uhi, Ulo, in, h, par, s);
+    Vec3<double> r;
+    if (self) {
+        Vec3<double> v = load_vec(self, h);
+#pragma unroll
+        for (int a = 0; a < 3; a++) r.c[a] = c * v.c[a] + scale * acc.c[a];
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; a++) r.c[a] = scale * acc.c[a];
+    }
+    st_vec(out, h, r);
+}
+
 static int hop_dispatch(stag_ctx* ctx, int prec, const void* in, void* out, int par, double scale, double c,
                         const void* self, cudaStream_t s) {
     switch (prec) {
+    case STAG_PREC_F64FF:
+        k_hop_ff<<<nblocks(ctx->g.Vh, HOP_TPB), HOP_TPB, 0, s>>>(ctx->g, ctx->U32, ctx->U32lo, (const double2*)in,
+                                                                (double2*)out, par, scale, c, (const double2*)self);
+        break;
     case STAG_PREC_F64: launch_hop<double, LP64>(ctx, ctx->U64, in, out, par, scale, c, self, s); break;
     case STAG_PREC_F32: launch_hop<float, LP32>(ctx, ctx->U32, in, out, par, (float)scale, (float)c, self, s); break;
     case STAG_PREC_BF16: launch_hop<float, LP16>(ctx, ctx->U16, in, out, par, (float)scale, (float)c, self, s); break;

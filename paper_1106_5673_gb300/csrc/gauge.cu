@@ -8,7 +8,7 @@ static const int TPB = 256;
 
 // ---------------------------------------------------------------- layout conversion
 
-__global__ void k_gauge_from_canonical(Geom g, const double* __restrict__ in, double2* U64, float4* U32,
+__global__ void k_gauge_from_canonical(Geom g, const double* __restrict__ in, double2* U64, float4* U32, float4* U32lo,
                                        uint2* U16) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * g.V) return;
@@ -21,7 +21,7 @@ __global__ void k_gauge_from_canonical(Geom g, const double* __restrict__ in, do
         for (int b = 0; b < 3; b++) u.e[a][b] = cmk(p[2 * (3 * a + b)], p[2 * (3 * a + b) + 1]);
     int par = par_of_lex(g, lex);
     store_link64(U64, g, mu, par, lex >> 1, u);
-    store_link_lowp(U32, U16, g, mu, par, lex >> 1, u);
+    store_link_lowp(U32, U32lo, U16, g, mu, par, lex >> 1, u);
 }
 
 __global__ void k_gauge_to_canonical(Geom g, const double2* __restrict__ U64, double* out) {
@@ -61,7 +61,7 @@ __global__ void k_mom_to_canonical(Geom g, const double* __restrict__ mom, doubl
 }
 
 int gauge_from_canonical(stag_ctx* ctx, const double* dev_links, cudaStream_t s) {
-    k_gauge_from_canonical<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, dev_links, ctx->U64, ctx->U32,
+    k_gauge_from_canonical<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, dev_links, ctx->U64, ctx->U32, ctx->U32lo,
                                                                       ctx->U16);
     STAG_LAUNCH_CHECK(ctx, "gauge_from_canonical");
     return STAG_OK;
@@ -302,7 +302,7 @@ STAG_D void reunitarize(Mat3<double>& u) {
 }
 
 // U <- exp(i eps P) U, reunitarised, in FP64; refreshes the FP32/BF16 copies
-__global__ void k_update_links(Geom g, double eps, const double* __restrict__ mom, double2* U64, float4* U32,
+__global__ void k_update_links(Geom g, double eps, const double* __restrict__ mom, double2* U64, float4* U32, float4* U32lo,
                                uint2* U16) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * g.V) return;
@@ -319,27 +319,27 @@ __global__ void k_update_links(Geom g, double eps, const double* __restrict__ mo
     Mat3<double> nu = mmul(E, u);
     reunitarize(nu);
     store_link64(U64, g, mu, par, h, nu);
-    store_link_lowp(U32, U16, g, mu, par, h, nu);
+    store_link_lowp(U32, U32lo, U16, g, mu, par, h, nu);
 }
 
 int update_links(stag_ctx* ctx, double eps, cudaStream_t s) {
-    k_update_links<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, eps, ctx->mom, ctx->U64, ctx->U32,
+    k_update_links<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, eps, ctx->mom, ctx->U64, ctx->U32, ctx->U32lo,
                                                               ctx->U16);
     STAG_LAUNCH_CHECK(ctx, "update_links");
     return STAG_OK;
 }
 
 // rebuild the FP32/BF16 copies from the FP64 master (after a Metropolis reject)
-__global__ void k_refresh_lowp(Geom g, const double2* __restrict__ U64, float4* U32, uint2* U16) {
+__global__ void k_refresh_lowp(Geom g, const double2* __restrict__ U64, float4* U32, float4* U32lo, uint2* U16) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 4 * g.V) return;
     int h = i % g.Vh, mp = i / g.Vh;
     Mat3<double> u = load_link64(U64, g, mp >> 1, mp & 1, h);
-    store_link_lowp(U32, U16, g, mp >> 1, mp & 1, h, u);
+    store_link_lowp(U32, U32lo, U16, g, mp >> 1, mp & 1, h, u);
 }
 
 int refresh_lowp_links(stag_ctx* ctx, cudaStream_t s) {
-    k_refresh_lowp<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, ctx->U64, ctx->U32, ctx->U16);
+    k_refresh_lowp<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, ctx->U64, ctx->U32, ctx->U32lo, ctx->U16);
     STAG_LAUNCH_CHECK(ctx, "refresh_lowp");
     return STAG_OK;
 }

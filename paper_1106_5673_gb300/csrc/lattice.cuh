@@ -259,15 +259,23 @@ STAG_D uint32_t pack_bf2(float lo, float hi) {
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// write the low-precision copies of one link from its FP64 rows 0,1
-STAG_D void store_link_lowp(float4* U32, uint2* U16, const Geom& g, int mu, int par, int h,
+// write the low-precision copies of one link from its FP64 rows 0,1: FP32
+// (U32 = fl32(u)), its FP32 residual (U32lo = fl32(u - U32), the low word of
+// the float-float pair) and BF16
+STAG_D void store_link_lowp(float4* U32, float4* U32lo, uint2* U16, const Geom& g, int mu, int par, int h,
                             const Mat3<double>& u) {
     size_t base = (size_t)(mu * 2 + par) * 3 * g.Vh + h;
-    float v[12] = {(float)u.e[0][0].re, (float)u.e[0][0].im, (float)u.e[0][1].re, (float)u.e[0][1].im,
-                   (float)u.e[0][2].re, (float)u.e[0][2].im, (float)u.e[1][0].re, (float)u.e[1][0].im,
-                   (float)u.e[1][1].re, (float)u.e[1][1].im, (float)u.e[1][2].re, (float)u.e[1][2].im};
+    const double d[12] = {u.e[0][0].re, u.e[0][0].im, u.e[0][1].re, u.e[0][1].im, u.e[0][2].re, u.e[0][2].im,
+                          u.e[1][0].re, u.e[1][0].im, u.e[1][1].re, u.e[1][1].im, u.e[1][2].re, u.e[1][2].im};
+    float v[12], w[12];
+#pragma unroll
+    for (int i = 0; i < 12; i++) {
+        v[i] = __double2float_rn(d[i]);
+        w[i] = __double2float_rn(d[i] - (double)v[i]);
+    }
 #pragma unroll
     for (int j = 0; j < 3; j++) {
+        U32lo[base + (size_t)j * g.Vh] = make_float4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
         U32[base + (size_t)j * g.Vh] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         U16[base + (size_t)j * g.Vh] = make_uint2(pack_bf2(v[4 * j], v[4 * j + 1]),
                                                   pack_bf2(v[4 * j + 2], v[4 * j + 3]));
@@ -356,6 +364,38 @@ STAG_D double block_sum(double v) {
         s = warp_sum(s);
     }
     return s;
+}
+
+// Block-wide sums of N values at once (one pair of barriers for all of them);
+// results valid in thread 0.  blockDim.x a multiple of 32, <= 1024.
+template <int N> STAG_D void block_sum_n(double v[N]) {
+    __shared__ double red_n[32][N];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < N; j++) v[j] = warp_sum(v[j]);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < N; j++) red_n[w][j] = v[j];
+    __syncthreads();
+    if (w == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+        for (int j = 0; j < N; j++) v[j] = warp_sum(lane < nw ? red_n[lane][j] : 0.0);
+    }
+}
+
+// In the last block: out[s] = sum_i partials[s * nb + i] for s < nseries,
+// one warp per series (all warps in parallel).  Ends with a barrier.
+STAG_D void reduce_series(const double* partials, int nseries, int nb, double* out_shared) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int sidx = w; sidx < nseries; sidx += nw) {
+        double v = 0.0;
+        for (int i = lane; i < nb; i += 32) v += __ldcg(partials + (size_t)sidx * nb + i);
+        v = warp_sum(v);
+        if (lane == 0) out_shared[sidx] = v;
+    }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------- shared helpers

@@ -1,0 +1,572 @@
+// refine.cu -- batched mixed-precision refinement of the shifted solutions.
+//
+// After the FP32 shifted CG, every shift whose FP64-accurate true residual
+// is above tolerance gets its own CG on (M_ee + s_k) e = r_k, all advanced
+// together: each kernel covers every active right-hand side, and the two
+// hops are multi-RHS hops that load each link once for a group of NR
+// right-hand sides (the batching of the spec design).  The recursion
+// runs in FP32 (or with BF16 links); reliable updates (x += x_lo in FP64,
+// r = b - (M + s_k) x recomputed FP64-accurately with the float-float
+// operator) happen at the host's polling points, every `chunk` iterations,
+// for the right-hand sides whose residual fell by `delta` since their last
+// update or that claim convergence.  A right-hand side leaves the batch only
+// after a true-residual check below tolerance.
+//
+// Per iteration:  A  t_k = D_oe p_k          (multi-RHS hop)
+//                 B  w_k = c_k p_k - D_eo t_k, alpha_k = rr_k / <p_k, w_k>
+//                 C  r_k -= alpha_k w_k, x_k += alpha_k p_k, rr_k, beta_k;
+//                    right-hand sides whose rr_k <= tol^2 |b|^2 are parked
+//                 D  p_k = r_k + beta_k p_k
+#include "hop.cuh"
+#include "stag_internal.h"
+
+#include <math.h>
+#include <stdlib.h>
+
+namespace {
+
+const int HOP_TPB = 128;
+const int BLAS_TPB = 256;
+const int NR = 4;  // right-hand sides per thread in the multi-RHS hops
+
+STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
+    __shared__ bool am_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(counter, 1u);
+        am_last = (t == nblocks_total - 1);
+    }
+    __syncthreads();
+    if (am_last && threadIdx.x == 0) *counter = 0;
+    return am_last;
+}
+
+template <int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
+                                                 float2* __restrict__ T, size_t stride, const BCGState* st) {
+    if (!st->live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q0 = blockIdx.y * NR, nact = st->n_act;
+    if (h >= g.Vh || q0 >= nact) return;
+    const int nj = min(NR, nact - q0);
+    int js[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) js[q] = (q < nj) ? st->act[q0 + q] : 0;
+    const Site s = site_of(g, h, 1);
+    Vec3<float> acc[NR];
+    hop2_multi<LP, NR>(g, U, P, stride, js, nj, h, 1, s, acc);
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+        if (q < nj) {
+#pragma unroll
+            for (int a = 0; a < 3; a++) acc[q].c[a] = 0.5f * acc[q].c[a];
+            st_vec(T + js[q] * stride, h, acc[q]);
+        }
+    }
+}
+
+template <int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_b_B(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
+                                                 const float2* __restrict__ P, float2* __restrict__ W, size_t stride,
+                                                 BCGState* st, double* partials, unsigned int* counter) {
+    if (!st->live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q0 = blockIdx.y * NR, nact = st->n_act;
+    const int nj = max(0, min(NR, nact - q0));
+    int js[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) js[q] = (q < nj) ? st->act[q0 + q] : 0;
+    double pw[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) pw[q] = 0.0;
+    if (h < g.Vh && nj > 0) {
+        const Site s = site_of(g, h, 0);
+        Vec3<float> acc[NR];
+        hop2_multi<LP, NR>(g, U, T, stride, js, nj, h, 0, s, acc);
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            if (q < nj) {
+                const float c = (float)st->c0[js[q]];
+                const Vec3<float> pv = load_vec(P + js[q] * stride, h);
+                Vec3<float> r;
+                float d = 0.f;
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    r.c[a] = c * pv.c[a] - 0.5f * acc[q].c[a];
+                    d += pv.c[a].re * r.c[a].re + pv.c[a].im * r.c[a].im;
+                }
+                st_vec(W + js[q] * stride, h, r);
+                pw[q] = (double)d;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+        const double bs = block_sum(pw[q]);
+        if (threadIdx.x == 0 && q < nj) partials[(size_t)(q0 + q) * gridDim.x + blockIdx.x] = bs;
+    }
+    if (last_block_n(counter, gridDim.x * gridDim.y)) {
+        for (int a = 0; a < nact; a++) {
+            double tot = 0.0;
+            for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + (size_t)a * gridDim.x + i);
+            tot = block_sum(tot);
+            if (threadIdx.x == 0) {
+                const int k = st->act[a];
+                st->alpha[k] = st->rr[k] / tot;
+            }
+        }
+    }
+}
+
+__global__ void k_b_C(long n, size_t stride, float2* __restrict__ R, const float2* __restrict__ W,
+                      const float2* __restrict__ P, float2* __restrict__ XL, BCGState* st, double* partials,
+                      unsigned int* counter) {
+    if (!st->live) return;
+    const int a = blockIdx.y, nact = st->n_act;
+    double acc = 0.0;
+    if (a < nact) {
+        const int k = st->act[a];
+        const float alpha = (float)st->alpha[k];
+        float2* r = R + k * stride;
+        const float2* w = W + k * stride;
+        const float2* p = P + k * stride;
+        float2* x = XL + k * stride;
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+            float2 rv = r[i];
+            const float2 wv = w[i], pv = p[i];
+            float2 xv = x[i];
+            rv.x -= alpha * wv.x;
+            rv.y -= alpha * wv.y;
+            xv.x += alpha * pv.x;
+            xv.y += alpha * pv.y;
+            r[i] = rv;
+            x[i] = xv;
+            acc += (double)(rv.x * rv.x + rv.y * rv.y);
+        }
+    }
+    const double bs = block_sum(acc);
+    if (threadIdx.x == 0 && a < nact) partials[(size_t)a * gridDim.x + blockIdx.x] = bs;
+    if (last_block_n(counter, gridDim.x * gridDim.y)) {
+        __shared__ double s_rr[STAG_MAXSHIFT];
+        for (int b = 0; b < nact; b++) {
+            double tot = 0.0;
+            for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + (size_t)b * gridDim.x + i);
+            tot = block_sum(tot);
+            if (threadIdx.x == 0) s_rr[b] = tot;
+        }
+        if (threadIdx.x == 0) {
+            int keep = 0, bad = 0, capped = 0;
+            for (int b = 0; b < nact; b++) {
+                const int k = st->act[b];
+                const double rr_new = s_rr[b];
+                st->iter[k] += 1;
+                st->beta[k] = rr_new / st->rr[k];
+                st->rr_prev[k] = st->rr[k];
+                st->rr[k] = rr_new;
+                if (!isfinite(rr_new)) bad = 1;
+                if (st->iter[k] >= st->maxit) capped = 1;
+                if (rr_new <= st->tol2bb) {
+                    st->want_rel[k] = 1;  // parked until the host checks it
+                } else {
+                    st->act[keep++] = k;
+                }
+            }
+            st->n_act = keep;
+            if (bad) st->nonfinite = 1;
+            st->stop_next = (keep == 0 || bad || capped) ? 1 : 0;
+        }
+    }
+}
+
+__global__ void k_b_D(long n, size_t stride, const float2* __restrict__ R, float2* __restrict__ P, BCGState* st,
+                      unsigned int* counter) {
+    if (!st->live) return;
+    const int a = blockIdx.y;
+    if (a < st->n_act) {
+        const int k = st->act[a];
+        const float beta = (float)st->beta[k];
+        const float2* r = R + k * stride;
+        float2* p = P + k * stride;
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+            const float2 rv = r[i];
+            float2 pv = p[i];
+            pv.x = rv.x + beta * pv.x;
+            pv.y = rv.y + beta * pv.y;
+            p[i] = pv;
+        }
+    }
+    if (last_block_n(counter, gridDim.x * gridDim.y)) {
+        if (threadIdx.x == 0 && st->stop_next) st->live = 0;
+    }
+}
+
+// ---- fused variant (3 kernels per iteration): B3 forms <p,w>, <r,w>, <w,w> per
+// right-hand side; its last block computes alpha_k, |r_k - alpha_k w_k|^2 by
+// expansion, beta_k and the parking; CD applies r -= alpha w, x += alpha p and
+// (for right-hand sides still active) p = r + beta p.
+template <int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_b_B3(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
+                                                  const float2* __restrict__ P, const float2* __restrict__ R,
+                                                  float2* __restrict__ W, size_t stride, BCGState* st,
+                                                  double* partials, unsigned int* counter) {
+    if (!st->live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q0 = blockIdx.y * NR, nact = st->n_act;
+    const int nj = max(0, min(NR, nact - q0));
+    int js[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) js[q] = (q < nj) ? st->act[q0 + q] : 0;
+    double sums[NR][4];
+#pragma unroll
+    for (int q = 0; q < NR; q++) sums[q][0] = sums[q][1] = sums[q][2] = sums[q][3] = 0.0;
+    if (h < g.Vh && nj > 0) {
+        const Site s = site_of(g, h, 0);
+        Vec3<float> acc[NR];
+        hop2_multi<LP, NR>(g, U, T, stride, js, nj, h, 0, s, acc);
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            if (q < nj) {
+                const float c = (float)st->c0[js[q]];
+                const Vec3<float> pv = load_vec(P + js[q] * stride, h), rv = load_vec(R + js[q] * stride, h);
+                Vec3<float> w;
+                float a = 0.f, b = 0.f, d = 0.f, e = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; i++) {
+                    w.c[i] = c * pv.c[i] - 0.5f * acc[q].c[i];
+                    a += pv.c[i].re * w.c[i].re + pv.c[i].im * w.c[i].im;
+                    b += rv.c[i].re * w.c[i].re + rv.c[i].im * w.c[i].im;
+                    d += w.c[i].re * w.c[i].re + w.c[i].im * w.c[i].im;
+                    e += rv.c[i].re * rv.c[i].re + rv.c[i].im * rv.c[i].im;
+                }
+                st_vec(W + js[q] * stride, h, w);
+                sums[q][0] = a;
+                sums[q][1] = b;
+                sums[q][2] = d;
+                sums[q][3] = e;
+            }
+        }
+    }
+    const size_t nbx = gridDim.x;
+    double flat[NR * 4];
+#pragma unroll
+    for (int q = 0; q < NR; q++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) flat[q * 4 + j] = sums[q][j];
+    block_sum_n<NR * 4>(flat);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int q = 0; q < NR; q++)
+            if (q < nj)
+#pragma unroll
+                for (int j = 0; j < 4; j++) partials[((size_t)(q0 + q) * 4 + j) * nbx + blockIdx.x] = flat[q * 4 + j];
+    if (last_block_n(counter, gridDim.x * gridDim.y)) {
+        __shared__ double s_sum[STAG_MAXSHIFT][4];
+        reduce_series(partials, nact * 4, (int)nbx, &s_sum[0][0]);
+        if (threadIdx.x == 0) {
+            int keep = 0, bad = 0, capped = 0;
+            for (int a = 0; a < nact; a++) {
+                const int k = st->act[a];
+                st->uact[a] = k;
+                const double rr = s_sum[a][3];  // fresh |r_k|^2 of this iteration
+                const double alpha = rr / s_sum[a][0];
+                double rr_new = rr - 2.0 * alpha * s_sum[a][1] + alpha * alpha * s_sum[a][2];
+                if (rr_new < 0.0) rr_new = 0.0;
+                st->alpha[k] = alpha;
+                st->beta[k] = rr_new / rr;
+                st->rr_prev[k] = rr;
+                st->rr[k] = rr_new;
+                st->iter[k] += 1;
+                if (!isfinite(rr_new) || !isfinite(alpha)) bad = 1;
+                if (st->iter[k] >= st->maxit) capped = 1;
+                if (rr_new <= st->tol2bb)
+                    st->want_rel[k] = 1;  // parked until the host checks it
+                else
+                    st->act[keep++] = k;
+            }
+            st->n_uact = nact;
+            st->n_act = keep;
+            if (bad) st->nonfinite = 1;
+            st->stop_next = (keep == 0 || bad || capped) ? 1 : 0;
+        }
+    }
+}
+
+__global__ void k_b_CD(long n, size_t stride, float2* __restrict__ R, const float2* __restrict__ W,
+                       float2* __restrict__ P, float2* __restrict__ XL, BCGState* st, unsigned int* counter) {
+    if (!st->live) return;
+    const int a = blockIdx.y;
+    if (a < st->n_uact) {
+        const int k = st->uact[a];
+        const float alpha = (float)st->alpha[k], beta = (float)st->beta[k];
+        const bool upd_p = !st->want_rel[k];
+        float2* r = R + k * stride;
+        const float2* w = W + k * stride;
+        float2* p = P + k * stride;
+        float2* x = XL + k * stride;
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+            float2 rv = r[i], pv = p[i], xv = x[i];
+            const float2 wv = w[i];
+            rv.x -= alpha * wv.x;
+            rv.y -= alpha * wv.y;
+            xv.x += alpha * pv.x;
+            xv.y += alpha * pv.y;
+            r[i] = rv;
+            x[i] = xv;
+            if (upd_p) {
+                pv.x = rv.x + beta * pv.x;
+                pv.y = rv.y + beta * pv.y;
+                p[i] = pv;
+            }
+        }
+    }
+    if (last_block_n(counter, gridDim.x * gridDim.y)) {
+        if (threadIdx.x == 0 && st->stop_next) st->live = 0;
+    }
+}
+
+// x_k += xl_k (FP64), xl_k = 0, for the listed slots
+struct SlotList {
+    int k[STAG_MAXSHIFT];
+};
+__global__ void k_b_accumulate(long n, size_t stride, double2* X, float2* XL, SlotList L) {
+    const int k = L.k[blockIdx.y];
+    double2* x = X + k * stride;
+    float2* xl = XL + k * stride;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float2 v = xl[i];
+        double2 d = x[i];
+        d.x += (double)v.x;
+        d.y += (double)v.y;
+        x[i] = d;
+        xl[i] = make_float2(0.f, 0.f);
+    }
+}
+
+// r_k = b - w (FP64 in, FP32 out), |r|^2 -> dst
+__global__ void k_b_residual(long n, const double2* __restrict__ b, const double2* __restrict__ w, float2* r,
+                             double* partials, unsigned int* counter, double* dst) {
+    double acc = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double2 bv = b[i], wv = w[i];
+        const double rx = bv.x - wv.x, ry = bv.y - wv.y;
+        r[i] = make_float2((float)rx, (float)ry);
+        acc += rx * rx + ry * ry;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+    if (last_block(counter)) finish_sum(partials, gridDim.x, dst);
+}
+
+__global__ void k_b_copy(long n, const float2* __restrict__ src, float2* dst) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+int env_i(const char* name, int dflt) {
+    const char* v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+double env_d(const char* name, double dflt) {
+    const char* v = getenv(name);
+    return v ? atof(v) : dflt;
+}
+
+}  // namespace
+
+// FP64-accurate residuals r_k = b - (M + s_k) x_k for the listed shifts with
+// the float-float operator: FP32 copies into R + k*n3, |r_k|^2 into
+// dscal[100 + k] (read back, synchronising).
+int batched_true_residuals(stag_ctx* ctx, double mass, const double* shifts, const int* ks, int nk, const double2* b,
+                           const double2* X, float2* R, double* rr_out, cudaStream_t s) {
+    const long n3 = 3L * ctx->g.Vh;
+    double2* w64 = (double2*)ws_get(ctx, WS_W64, sizeof(double2) * n3);
+    double2* t64 = (double2*)ws_get(ctx, WS_T64, sizeof(double2) * n3);
+    if (!w64 || !t64) return stag_fail(ctx, STAG_ERR_OOM, "residual workspace");
+    for (int i = 0; i < nk; i++) {
+        const int k = ks[i];
+        int st = mee_apply(ctx, STAG_PREC_F64FF, mass * mass + shifts[k], X + k * n3, w64, t64, s);
+        if (st) return st;
+        k_b_residual<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, b, w64, R + k * n3, ctx->partials, ctx->counter,
+                                                           ctx->dscal + 100 + k);
+        STAG_LAUNCH_CHECK(ctx, "batched residual");
+    }
+    // scalars 0..100+MAXSHIFT: also brings |b|^2 (slot 1) to the host
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * (100 + STAG_MAXSHIFT),
+                                   cudaMemcpyDeviceToHost, s));
+    STAG_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int i = 0; i < nk; i++) rr_out[ks[i]] = ctx->hscal[100 + ks[i]];
+    return STAG_OK;
+}
+
+int run_graph_chunk(stag_ctx* ctx, const char* key, int nkernels, void (*enqueue)(stag_ctx*, void*, cudaStream_t),
+                    void* arg, cudaStream_t s);
+
+namespace {
+struct BIter {
+    int lp;
+    Links U;
+    float2 *R, *P, *W, *T, *XL;
+    double* part;
+    int ny_hop, ny_blas, chunk, fused;
+};
+
+void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
+    const BIter& a = *(const BIter*)argp;
+    const Geom& g = ctx->g;
+    const long n3 = 3L * g.Vh;
+    const size_t stride = (size_t)n3;
+    const dim3 gh(nblocks(g.Vh, HOP_TPB), a.ny_hop), gb(ctx->num_sms, a.ny_blas);
+    for (int i = 0; i < a.chunk; i++) {
+        if (a.fused) {
+            if (a.lp == LP32) {
+                k_b_A<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+                k_b_B3<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
+                                                     ctx->counter);
+            } else {
+                k_b_A<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+                k_b_B3<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
+                                                     ctx->counter);
+            }
+            k_b_CD<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, ctx->counter);
+            continue;
+        }
+        if (a.lp == LP32) {
+            k_b_A<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+            k_b_B<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
+        } else {
+            k_b_A<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+            k_b_B<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
+        }
+        k_b_C<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, a.part, ctx->counter);
+        k_b_D<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.P, ctx->bcg, ctx->counter);
+    }
+}
+}  // namespace
+
+// Refines the FP64 solutions X + k*n3 for the shifts ks[0..nk) (those whose
+// true residual rr[k] > tol^2 |b|^2 on entry; R + k*n3 must already hold
+// their FP32 residuals).  On return rr[k] holds each shift's final
+// FP64-accurate true residual^2.
+int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, const int* ks, int nk, const double2* b,
+                   double bb, double2* X, float2* R, double tol, int maxit, double* rr, int* iters, int* reliable,
+                   int* matvecs, cudaStream_t s) {
+    const Geom& g = ctx->g;
+    const long n3 = 3L * g.Vh;
+    const size_t vb = sizeof(float2) * n3 * STAG_MAXSHIFT;
+    BIter it;
+    it.lp = lp;
+    it.U.u = (lp == LP32) ? (const void*)ctx->U32 : (const void*)ctx->U16;
+    it.U.lo = ctx->U32lo;
+    it.R = R;
+    it.P = (float2*)ws_get(ctx, WS_PK32, vb);
+    it.XL = (float2*)ws_get(ctx, WS_XK32, vb);
+    it.W = (float2*)ws_get(ctx, WS_BW, vb);
+    it.T = (float2*)ws_get(ctx, WS_BT, vb);
+    const int nbx = nblocks(g.Vh, HOP_TPB);
+    it.part = (double*)ws_get(ctx, WS_BPART,
+                              sizeof(double) * 4 * STAG_MAXSHIFT * (size_t)(nbx > ctx->num_sms ? nbx : ctx->num_sms));
+    if (!it.P || !it.XL || !it.W || !it.T || !it.part) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
+    it.ny_hop = (nk + NR - 1) / NR;
+    it.ny_blas = nk;
+    it.chunk = env_i("STAG_CHUNK", 16);
+    it.fused = env_i("STAG_FUSED", 1);
+    const double delta = env_d("STAG_RELIABLE_DELTA", 0.1);
+    const double tol2bb = tol * tol * bb;
+    const int trace = env_i("STAG_TRACE_REFINE", 0);
+
+    BCGState* hs = ctx->bcg_host;
+    memset(hs, 0, sizeof(BCGState));
+    for (int i = 0; i < nk; i++) {
+        const int k = ks[i];
+        hs->act[i] = k;
+        hs->rr[k] = hs->rr_max[k] = rr[k];
+        hs->c0[k] = mass * mass + shifts[k];
+        STAG_CUDA(ctx, cudaMemsetAsync(it.XL + k * n3, 0, sizeof(float2) * n3, s));
+        k_b_copy<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, R + k * n3, it.P + k * n3);
+        STAG_LAUNCH_CHECK(ctx, "refine init");
+    }
+    hs->n_act = nk;
+    hs->tol2bb = tol2bb;
+    hs->delta2 = delta * delta;
+    hs->maxit = maxit;
+    hs->live = nk > 0;
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->bcg, hs, sizeof(BCGState), cudaMemcpyHostToDevice, s));
+
+    char key[64];
+    snprintf(key, sizeof key, "bcg_%d_%d_%d_%d", lp, nk, it.chunk, it.fused);
+    int remaining = nk;
+    int done[STAG_MAXSHIFT] = {0};
+    while (remaining > 0) {
+        int st = run_graph_chunk(ctx, key, (it.fused ? 3 : 4) * it.chunk, enqueue_b, &it, s);
+        if (st) return st;
+        STAG_CUDA(ctx, cudaMemcpyAsync(hs, ctx->bcg, sizeof(BCGState), cudaMemcpyDeviceToHost, s));
+        STAG_CUDA(ctx, cudaStreamSynchronize(s));
+        if (trace) {
+            fprintf(stderr, "[refine] n_act %d live %d nonfinite %d |", hs->n_act, hs->live, hs->nonfinite);
+            for (int i = 0; i < nk; i++)
+                fprintf(stderr, " k%d it%d rr%.2e a%.2e b%.2e p%d", ks[i], hs->iter[ks[i]], hs->rr[ks[i]] / bb,
+                        hs->alpha[ks[i]], hs->beta[ks[i]], hs->want_rel[ks[i]]);
+            fprintf(stderr, "\n");
+        }
+        if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in batched CG");
+        // reliable updates: parked (claimed convergence) and those whose residual dropped by delta
+        int upd[STAG_MAXSHIFT], nu = 0, parked[STAG_MAXSHIFT] = {0};
+        int in_act[STAG_MAXSHIFT] = {0};
+        for (int a = 0; a < hs->n_act; a++) in_act[hs->act[a]] = 1;
+        for (int i = 0; i < nk; i++) {
+            const int k = ks[i];
+            if (done[k]) continue;
+            if (hs->want_rel[k]) {
+                parked[k] = 1;
+                upd[nu++] = k;
+            } else if (in_act[k] && hs->rr[k] > 1e2 * hs->rr_max[k]) {
+                parked[k] = 1;  // the recursion drifted away: restart from the true residual
+                upd[nu++] = k;
+            } else if (in_act[k] && (hs->rr[k] < hs->delta2 * hs->rr_max[k] || hs->iter[k] >= maxit)) {
+                upd[nu++] = k;
+            }
+        }
+        if (nu > 0) {
+            SlotList L;
+            for (int i = 0; i < nu; i++) L.k[i] = upd[i];
+            k_b_accumulate<<<dim3(ctx->num_sms, nu), BLAS_TPB, 0, s>>>(n3, (size_t)n3, X, it.XL, L);
+            STAG_LAUNCH_CHECK(ctx, "refine accumulate");
+            double rrt[STAG_MAXSHIFT];
+            if ((st = batched_true_residuals(ctx, mass, shifts, upd, nu, b, X, R, rrt, s))) return st;
+            *matvecs += nu;
+            *reliable += nu;
+            for (int i = 0; i < nu; i++) {
+                const int k = upd[i];
+                hs->want_rel[k] = 0;
+                rr[k] = rrt[k];
+                if (rrt[k] <= tol2bb || hs->iter[k] >= maxit) {
+                    done[k] = 1;
+                    remaining--;
+                    in_act[k] = 0;
+                    continue;
+                }
+                hs->rr[k] = hs->rr_max[k] = rrt[k];
+                if (parked[k]) {  // the recursion claimed convergence but the true residual disagrees: restart
+                    k_b_copy<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, R + k * n3, it.P + k * n3);
+                    STAG_LAUNCH_CHECK(ctx, "refine restart");
+                    in_act[k] = 1;
+                }
+            }
+        }
+        // rebuild the active list (compacted, stable order)
+        int na = 0;
+        for (int i = 0; i < nk; i++)
+            if (in_act[ks[i]] && !done[ks[i]]) hs->act[na++] = ks[i];
+        hs->n_act = na;
+        hs->stop_next = 0;
+        hs->live = na > 0;
+        if (remaining > 0 && na == 0) return stag_fail(ctx, STAG_ERR_NOCONV, "batched refinement stalled");
+        STAG_CUDA(ctx, cudaMemcpyAsync(ctx->bcg, hs, sizeof(BCGState), cudaMemcpyHostToDevice, s));
+    }
+    for (int i = 0; i < nk; i++) {
+        iters[ks[i]] = hs->iter[ks[i]];
+        *matvecs += hs->iter[ks[i]];
+    }
+    return STAG_OK;
+}

@@ -44,7 +44,7 @@ int rational_apply_int(stag_ctx* ctx, double mass, const stag_rational* r, const
 
 // F = total force dP/dtau = gauge force + sum_pf fermion force
 int total_force(stag_ctx* ctx, const stag_params* p, const TrajWork& w, long long* iters, cudaStream_t s) {
-    const int mixed = p->solve_mode_md != STAG_SOLVE_F64;
+    const int mixed = p->solve_mode_md == STAG_SOLVE_MIXED || p->solve_mode_md == STAG_SOLVE_MIXED_BF16;
     int st = gauge_force_internal_prec(ctx, p->beta, w.F, 0, mixed, s);
     if (st) return st;
     for (int pf = 0; pf < p->npf; pf++) {

@@ -32,17 +32,33 @@ static double env_dbl(const char* name, double dflt) {
     return v ? atof(v) : dflt;
 }
 
+// 3 kernels per shifted-CG iteration (A, B3, CD) unless STAG_FUSED=0
+static int fused_iter() {
+    static int f = -1;
+    if (f < 0) f = env_int("STAG_FUSED", 1);
+    return f;
+}
+
+static Links make_links(const stag_ctx* ctx, int lp) {
+    Links L;
+    L.lo = ctx->U32lo;
+    L.u = (lp == LP64) ? (const void*)ctx->U64
+          : (lp == LP32 || lp == LPFF) ? (const void*)ctx->U32
+                                       : (const void*)ctx->U16;
+    return L;
+}
+
 // ============================================================== multi-shift kernels
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_ms_A(Geom g, const void* __restrict__ U,
+__global__ void __launch_bounds__(HOP_TPB) k_ms_A(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ t, const int* live) {
     if (!*live) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= g.Vh) return;
     const Site s = site_of(g, h, 1);
-    Vec3<R> acc = hop2<R, LP>(g, U, p, h, 1, s);
+    Vec3<R> acc = hopL<R, LP>(g, U, p, h, 1, s);
 #pragma unroll
     for (int a = 0; a < 3; a++) acc.c[a] = (R)0.5 * acc.c[a];
     st_vec(t, h, acc);
@@ -50,12 +66,12 @@ __global__ void __launch_bounds__(HOP_TPB) k_ms_A(Geom g, const void* __restrict
 
 // w = c0 p - 1/2 hop(t) on even sites; returns Re<p, w> in FP64 via partials
 template <typename R, int LP>
-STAG_D double mee_second_hop(const Geom& g, const void* U, const typename VT<R>::T* t,
+STAG_D double mee_second_hop(const Geom& g, Links U, const typename VT<R>::T* t,
                              const typename VT<R>::T* p, typename VT<R>::T* w, R c0, int h) {
     double pw = 0.0;
     if (h < g.Vh) {
         const Site s = site_of(g, h, 0);
-        Vec3<R> acc = hop2<R, LP>(g, U, t, h, 0, s);
+        Vec3<R> acc = hopL<R, LP>(g, U, t, h, 0, s);
         Vec3<R> pv = load_vec(p, h);
         Vec3<R> r;
         R ppw = 0;
@@ -71,7 +87,7 @@ STAG_D double mee_second_hop(const Geom& g, const void* U, const typename VT<R>:
 }
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_ms_B(Geom g, const void* __restrict__ U,
+__global__ void __launch_bounds__(HOP_TPB) k_ms_B(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ t,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ w, MSState* st, double* partials,
@@ -85,26 +101,175 @@ __global__ void __launch_bounds__(HOP_TPB) k_ms_B(Geom g, const void* __restrict
         double tot = 0.0;
         for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + i);
         tot = block_sum(tot);
+        __shared__ double s_alpha;
         if (threadIdx.x == 0) {
             st->pw = tot;
-            const double alpha = st->rr / tot;
-            st->alpha = alpha;
-            const double s0 = st->shifts[st->base];
-            for (int k = 0; k < st->n; k++) {
-                if (st->active[k]) {
-                    const double d = st->shifts[k] - s0;
-                    const double den = st->zeta_old[k] * st->alpha_old * (1.0 + d * alpha) +
-                                       alpha * st->beta_old * (st->zeta_old[k] - st->zeta[k]);
-                    const double zn = st->zeta[k] * st->zeta_old[k] * st->alpha_old / den;
-                    st->zeta_next[k] = zn;
-                    st->ak[k] = alpha * zn / st->zeta[k];
-                    st->upd_x[k] = 1;
-                } else {
-                    st->upd_x[k] = 0;
-                    st->ak[k] = 0.0;
-                }
+            s_alpha = st->rr / tot;
+            st->alpha = s_alpha;
+        }
+        __syncthreads();
+        // one thread per shift: the zeta recurrences are independent
+        const int k = threadIdx.x;
+        if (k < st->n) {
+            const double alpha = s_alpha;
+            if (st->active[k]) {
+                const double d = st->shifts[k] - st->shifts[st->base];
+                const double zo = st->zeta_old[k], z = st->zeta[k], ao = st->alpha_old;
+                const double den = zo * ao * (1.0 + d * alpha) + alpha * st->beta_old * (zo - z);
+                const double zn = z * zo * ao / den;
+                st->zeta_next[k] = zn;
+                st->ak[k] = alpha * zn / z;
+                st->upd_x[k] = 1;
+            } else {
+                st->upd_x[k] = 0;
+                st->ak[k] = 0.0;
             }
         }
+    }
+}
+
+// ---- fused variant: 3 kernels per iteration (A, B3, CD)
+// B3: w = c0 p - D_eo t and the three sums <p,w>, <r,w>, <w,w>; the last block
+// forms alpha = rr/<p,w> and |r - alpha w|^2 = rr - 2 alpha <r,w> + alpha^2 <w,w>
+// (no separate pass over r), then every scalar of the iteration: the shifted
+// zeta, a_k, b_k, per-shift convergence and the stop flag.
+template <typename R, int LP>
+__global__ void __launch_bounds__(HOP_TPB) k_ms_B3(Geom g, Links U, const typename VT<R>::T* __restrict__ t,
+                                                   const typename VT<R>::T* __restrict__ p,
+                                                   const typename VT<R>::T* __restrict__ r,
+                                                   typename VT<R>::T* __restrict__ w, MSState* st, double* partials,
+                                                   unsigned int* counter) {
+    if (!st->live) return;
+    const int h = blockIdx.x * blockDim.x + threadIdx.x;
+    double pw = 0.0, rw = 0.0, ww = 0.0, rr = 0.0;
+    if (h < g.Vh) {
+        const Site s = site_of(g, h, 0);
+        const Vec3<R> acc = hopL<R, LP>(g, U, t, h, 0, s);
+        const Vec3<R> pv = load_vec(p, h), rv = load_vec(r, h);
+        const R c0 = (R)st->c0;
+        Vec3<R> wv;
+        R a = 0, b = 0, c = 0, d = 0;
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            wv.c[i] = c0 * pv.c[i] - (R)0.5 * acc.c[i];
+            a += pv.c[i].re * wv.c[i].re + pv.c[i].im * wv.c[i].im;
+            b += rv.c[i].re * wv.c[i].re + rv.c[i].im * wv.c[i].im;
+            c += wv.c[i].re * wv.c[i].re + wv.c[i].im * wv.c[i].im;
+            d += rv.c[i].re * rv.c[i].re + rv.c[i].im * rv.c[i].im;
+        }
+        st_vec(w, h, wv);
+        pw = (double)a;
+        rw = (double)b;
+        ww = (double)c;
+        rr = (double)d;
+    }
+    double v[4] = {pw, rw, ww, rr};
+    block_sum_n<4>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) partials[j * gridDim.x + blockIdx.x] = v[j];
+    }
+    if (last_block(counter)) {
+        __shared__ double s_t[4];
+        reduce_series(partials, 4, gridDim.x, s_t);
+        const double t0 = s_t[0], t1 = s_t[1], t2 = s_t[2], t3 = s_t[3];
+        __shared__ double s_alpha, s_beta, s_rr;
+        __shared__ int s_iter;
+        if (threadIdx.x == 0) {
+            // |r_j|^2 freshly reduced (t3), so the expansion of |r_{j+1}|^2
+            // carries one step of rounding, not an accumulated recursion
+            const double alpha = t3 / t0;
+            double rr_new = t3 - 2.0 * alpha * t1 + alpha * alpha * t2;
+            if (rr_new < 0.0) rr_new = 0.0;
+            s_alpha = alpha;
+            s_rr = rr_new;
+            s_beta = rr_new / t3;
+            s_iter = st->iter + 1;
+            st->pw = t0;
+            st->alpha = alpha;
+        }
+        __syncthreads();
+        const int k = threadIdx.x;
+        int act = 0;
+        if (k < st->n) {
+            if (st->active[k]) {
+                const double alpha = s_alpha;
+                const double d = st->shifts[k] - st->shifts[st->base];
+                const double zo = st->zeta_old[k], z = st->zeta[k], ao = st->alpha_old;
+                const double den = zo * ao * (1.0 + d * alpha) + alpha * st->beta_old * (zo - z);
+                const double zn = z * zo * ao / den;
+                const double ratio = zn / z;
+                st->ak[k] = alpha * ratio;
+                st->bk[k] = s_beta * ratio * ratio;
+                st->zeta_old[k] = z;
+                st->zeta[k] = zn;
+                st->upd_x[k] = 1;
+                st->iters_shift[k] = s_iter;
+                st->active[k] = (zn * zn * s_rr > st->tol2bb) ? 1 : 0;
+            } else {
+                st->upd_x[k] = 0;
+                st->ak[k] = 0.0;
+            }
+            act = st->active[k];
+        }
+        const int n_active = __syncthreads_count(act);
+        if (threadIdx.x == 0) {
+            st->iter = s_iter;
+            st->n_active = n_active;
+            st->beta = s_beta;
+            st->rr = s_rr;
+            st->alpha_old = s_alpha;
+            st->beta_old = s_beta;
+            const int bad = !isfinite(s_rr) || !isfinite(s_beta) || !isfinite(s_alpha);
+            if (bad) st->nonfinite = 1;
+            st->stop_next = (n_active == 0 || s_iter >= st->maxit || bad) ? 1 : 0;
+        }
+    }
+}
+
+// CD: r -= alpha w; p = r + beta p; x_k += a_k p_k; p_k = zeta_k r + b_k p_k
+template <typename V2, typename R>
+__global__ void k_ms_CD(long n, long stride, V2* __restrict__ r, const V2* __restrict__ w, V2* __restrict__ p,
+                        V2* __restrict__ pk, V2* __restrict__ xk, MSState* st, unsigned int* counter) {
+    if (!st->live) return;
+    __shared__ R s_ak[STAG_MAXSHIFT], s_bk[STAG_MAXSHIFT], s_z[STAG_MAXSHIFT];
+    __shared__ int s_ux[STAG_MAXSHIFT], s_act[STAG_MAXSHIFT];
+    const int ns = st->n;
+    if (threadIdx.x < ns) {
+        s_ak[threadIdx.x] = (R)st->ak[threadIdx.x];
+        s_bk[threadIdx.x] = (R)st->bk[threadIdx.x];
+        s_z[threadIdx.x] = (R)st->zeta[threadIdx.x];
+        s_ux[threadIdx.x] = st->upd_x[threadIdx.x];
+        s_act[threadIdx.x] = st->active[threadIdx.x];
+    }
+    __syncthreads();
+    const R alpha = (R)st->alpha, beta = (R)st->beta;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        V2 rv = r[i];
+        const V2 wv = w[i];
+        rv.x -= alpha * wv.x;
+        rv.y -= alpha * wv.y;
+        r[i] = rv;
+        V2 pv = p[i];
+        pv.x = rv.x + beta * pv.x;
+        pv.y = rv.y + beta * pv.y;
+        p[i] = pv;
+        for (int k = 0; k < ns; k++) {
+            if (!s_ux[k]) continue;
+            V2 q = pk[k * stride + i];
+            V2 x = xk[k * stride + i];
+            x.x += s_ak[k] * q.x;
+            x.y += s_ak[k] * q.y;
+            xk[k * stride + i] = x;
+            if (s_act[k]) {
+                q.x = s_z[k] * rv.x + s_bk[k] * q.x;
+                q.y = s_z[k] * rv.y + s_bk[k] * q.y;
+                pk[k * stride + i] = q;
+            }
+        }
+    }
+    if (last_block(counter)) {
+        if (threadIdx.x == 0 && st->stop_next) st->live = 0;
     }
 }
 
@@ -127,22 +292,33 @@ __global__ void k_ms_C(long n, V2* __restrict__ r, const V2* __restrict__ w, MSS
         double tot = 0.0;
         for (int i = threadIdx.x; i < gridDim.x; i += blockDim.x) tot += __ldcg(partials + i);
         tot = block_sum(tot);
+        __shared__ double s_rr, s_beta;
+        __shared__ int s_iter;
         if (threadIdx.x == 0) {
-            const double rr_new = tot;
-            st->iter += 1;
-            const double beta = rr_new / st->rr;
-            int n_active = 0;
-            for (int k = 0; k < st->n; k++) {
-                if (st->upd_x[k]) {
-                    const double ratio = st->zeta_next[k] / st->zeta[k];
-                    st->bk[k] = beta * ratio * ratio;
-                    st->zeta_old[k] = st->zeta[k];
-                    st->zeta[k] = st->zeta_next[k];
-                    st->iters_shift[k] = st->iter;
-                    st->active[k] = (st->zeta[k] * st->zeta[k] * rr_new > st->tol2bb) ? 1 : 0;
-                }
-                n_active += st->active[k];
+            s_rr = tot;
+            s_beta = tot / st->rr;
+            s_iter = st->iter + 1;
+        }
+        __syncthreads();
+        // one thread per shift
+        const int k = threadIdx.x;
+        int act = 0;
+        if (k < st->n) {
+            if (st->upd_x[k]) {
+                const double zn = st->zeta_next[k], z = st->zeta[k];
+                const double ratio = zn / z;
+                st->bk[k] = s_beta * ratio * ratio;
+                st->zeta_old[k] = z;
+                st->zeta[k] = zn;
+                st->iters_shift[k] = s_iter;
+                st->active[k] = (zn * zn * s_rr > st->tol2bb) ? 1 : 0;
             }
+            act = st->active[k];
+        }
+        const int n_active = __syncthreads_count(act);
+        if (threadIdx.x == 0) {
+            const double rr_new = s_rr, beta = s_beta;
+            st->iter = s_iter;
             st->n_active = n_active;
             st->beta = beta;
             st->rr = rr_new;
@@ -150,7 +326,7 @@ __global__ void k_ms_C(long n, V2* __restrict__ r, const V2* __restrict__ w, MSS
             st->beta_old = beta;
             const int bad = !isfinite(rr_new) || !isfinite(beta);
             if (bad) st->nonfinite = 1;
-            st->stop_next = (n_active == 0 || st->iter >= st->maxit || bad) ? 1 : 0;
+            st->stop_next = (n_active == 0 || s_iter >= st->maxit || bad) ? 1 : 0;
         }
     }
 }
@@ -302,21 +478,21 @@ __global__ void k_cg_D(long n, const V2* __restrict__ r, V2* __restrict__ p, CGS
 }
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_cg_A(Geom g, const void* __restrict__ U,
+__global__ void __launch_bounds__(HOP_TPB) k_cg_A(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ t, const CGState* st) {
     if (!st->live) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= g.Vh) return;
     const Site s = site_of(g, h, 1);
-    Vec3<R> acc = hop2<R, LP>(g, U, p, h, 1, s);
+    Vec3<R> acc = hopL<R, LP>(g, U, p, h, 1, s);
 #pragma unroll
     for (int a = 0; a < 3; a++) acc.c[a] = (R)0.5 * acc.c[a];
     st_vec(t, h, acc);
 }
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_cg_B(Geom g, const void* __restrict__ U,
+__global__ void __launch_bounds__(HOP_TPB) k_cg_B(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ t,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ w, CGState* st, double* partials,
@@ -398,13 +574,20 @@ struct MSBufs {
 };
 
 template <typename R, int LP>
-void launch_ms_iter(stag_ctx* ctx, const void* U, const MSBufs& b, cudaStream_t s) {
+void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
     typedef typename VT<R>::T V2;
     const Geom& g = ctx->g;
     const long n = 3L * g.Vh;
     const int nb_hop = nblocks(g.Vh, HOP_TPB);
     const int nb_blas = ctx->num_sms * 4;
     k_ms_A<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, &ctx->ms->live);
+    if (fused_iter()) {
+        k_ms_B3<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
+                                                 ctx->ms, ctx->partials, ctx->counter);
+        k_ms_CD<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, (V2*)b.pk,
+                                                   (V2*)b.xk, ctx->ms, ctx->counter);
+        return;
+    }
     k_ms_B<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (V2*)b.w, ctx->ms,
                                             ctx->partials, ctx->counter);
     k_ms_C<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (V2*)b.r, (const V2*)b.w, ctx->ms, ctx->partials, ctx->counter);
@@ -413,7 +596,7 @@ void launch_ms_iter(stag_ctx* ctx, const void* U, const MSBufs& b, cudaStream_t 
 }
 
 template <typename R, int LP>
-void launch_cg_iter(stag_ctx* ctx, const void* U, void* r, void* p, void* w, void* t, void* x, cudaStream_t s) {
+void launch_cg_iter(stag_ctx* ctx, Links U, void* r, void* p, void* w, void* t, void* x, cudaStream_t s) {
     typedef typename VT<R>::T V2;
     const Geom& g = ctx->g;
     const long n = 3L * g.Vh;
@@ -473,10 +656,11 @@ int read_cg_state(stag_ctx* ctx, cudaStream_t s) {
     return STAG_OK;
 }
 
-// FP64 true residual |b - (M + shift) x|^2 into dscal[slot]; w, t FP64 scratch
-int true_residual2(stag_ctx* ctx, double c, const double2* b, const double2* x, double2* w, double2* t,
+// FP64-accurate true residual |b - (M + shift) x|^2 into *dst; the operator is
+// applied in native FP64 (prec F64) or float-float (prec F64FF); w, t FP64 scratch
+int true_residual2(stag_ctx* ctx, int prec, double c, const double2* b, const double2* x, double2* w, double2* t,
                    double2* r_out, float2* r_low, double* dst, cudaStream_t s) {
-    int st = mee_apply(ctx, STAG_PREC_F64, c, x, w, t, s);
+    int st = mee_apply(ctx, prec, c, x, w, t, s);
     if (st) return st;
     long n = 3L * ctx->g.Vh;
     k_residual<float2><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n, b, w, r_out, r_low, ctx->partials, ctx->counter,
@@ -504,7 +688,7 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
     bf.xk = ws_get(ctx, f64 ? WS_XK64 : WS_XK32, vb * STAG_MAXSHIFT);
     if (!bf.r || !bf.p || !bf.w || !bf.t || !bf.pk || !bf.xk) return stag_fail(ctx, STAG_ERR_OOM, "solver workspace");
     if (f64) bf.xk = xout;  // FP64: accumulate straight into the output
-    const void* U = (LP == LP64) ? (const void*)ctx->U64 : (LP == LP32) ? (const void*)ctx->U32 : (const void*)ctx->U16;
+    Links U = make_links(ctx, LP);
 
     // scalar state
     MSState* hs = ctx->ms_host;
@@ -523,10 +707,10 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
 
     const int chunk = env_int("STAG_CHUNK", 16);
     char key[64];
-    snprintf(key, sizeof key, "ms_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, bf.xk);
+    snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), bf.xk);
     int guard = 0;
     for (;;) {
-        st = run_chunk(ctx, key, 4 * chunk, [&](cudaStream_t cs) {
+        st = run_chunk(ctx, key, (fused_iter() ? 3 : 4) * chunk, [&](cudaStream_t cs) {
             for (int i = 0; i < chunk; i++) launch_ms_iter<R, LP>(ctx, U, bf, cs);
         }, s);
         if (st) return st;
@@ -563,14 +747,14 @@ int refine_shift(stag_ctx* ctx, double mass, double shift, const double2* b, dou
     double2* w64 = (double2*)ws_get(ctx, WS_W64, vb64);
     double2* t64 = (double2*)ws_get(ctx, WS_T64, vb64);
     if (!r32 || !p32 || !w32 || !t32 || !x32 || !w64 || !t64) return stag_fail(ctx, STAG_ERR_OOM, "refine workspace");
-    const void* U = (LP == LP32) ? (const void*)ctx->U32 : (const void*)ctx->U16;
+    Links U = make_links(ctx, LP);
     const double c = mass * mass + shift;
     const double delta = env_dbl("STAG_RELIABLE_DELTA", 0.1);
     const int chunk = env_int("STAG_CHUNK", 16);
     int st;
 
     double* dres = ctx->dscal + 0;
-    if ((st = true_residual2(ctx, c, b, x, w64, t64, nullptr, r32, dres, s))) return st;
+    if ((st = true_residual2(ctx, STAG_PREC_F64FF, c, b, x, w64, t64, nullptr, r32, dres, s))) return st;
     STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal, dres, sizeof(double), cudaMemcpyDeviceToHost, s));
     STAG_CUDA(ctx, cudaStreamSynchronize(s));
     double rr = ctx->hscal[0];
@@ -609,7 +793,7 @@ int refine_shift(stag_ctx* ctx, double mass, double shift, const double2* b, dou
         // reliable update: x += x_lo in FP64, true residual in FP64
         k_accumulate<float2><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, x, x32);
         STAG_LAUNCH_CHECK(ctx, "accumulate");
-        if ((st = true_residual2(ctx, c, b, x, w64, t64, nullptr, r32, dres, s))) return st;
+        if ((st = true_residual2(ctx, STAG_PREC_F64FF, c, b, x, w64, t64, nullptr, r32, dres, s))) return st;
         STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal, dres, sizeof(double), cudaMemcpyDeviceToHost, s));
         STAG_CUDA(ctx, cudaStreamSynchronize(s));
         *matvecs += 1;
@@ -638,6 +822,11 @@ int refine_shift(stag_ctx* ctx, double mass, double shift, const double2* b, dou
 
 }  // namespace
 
+int run_graph_chunk(stag_ctx* ctx, const char* key, int nkernels, void (*enqueue)(stag_ctx*, void*, cudaStream_t),
+                    void* arg, cudaStream_t s) {
+    return run_chunk(ctx, std::string(key), nkernels, [&](cudaStream_t cs) { enqueue(ctx, arg, cs); }, s);
+}
+
 int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src,
                      double2* const* sols, double tol, int maxit, int mode, stag_solve_info* info, cudaStream_t s) {
     if (n < 1 || n > STAG_MAXSHIFT) return stag_fail(ctx, STAG_ERR_ARG, "number of shifts %d out of range", n);
@@ -655,8 +844,11 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
     double2* X = (double2*)ws_get(ctx, WS_FX, vb64 * STAG_MAXSHIFT);
     if (!X) return stag_fail(ctx, STAG_ERR_OOM, "solution workspace");
     int st;
+    const int check_prec = (mode == STAG_SOLVE_F64) ? STAG_PREC_F64 : STAG_PREC_F64FF;
     if (mode == STAG_SOLVE_F64) {
         st = ms_core<double, LP64>(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
+    } else if (mode == STAG_SOLVE_F64FF) {
+        st = ms_core<double, LPFF>(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
     } else if (mode == STAG_SOLVE_MIXED || mode == STAG_SOLVE_MIXED_BF16) {
         const double tol_ms = fmax(tol, env_dbl("STAG_MS_TOL32", 1e-6));
         if (mode == STAG_SOLVE_MIXED)
@@ -668,12 +860,55 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
     }
     if (st) return st;
 
+    const int batched = (mode == STAG_SOLVE_MIXED || mode == STAG_SOLVE_MIXED_BF16) && env_int("STAG_BATCHED", 1);
+    if (batched) {
+        // FP64-accurate residuals of all shifts (float-float operator), then the
+        // batched refinement of those above tolerance
+        float2* R = (float2*)ws_get(ctx, WS_BR, sizeof(float2) * n3 * STAG_MAXSHIFT);
+        if (!R) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
+        if ((st = blas_dot_re(ctx, STAG_PREC_F64, src, src, ctx->dscal + 1, s))) return st;
+        int all[STAG_MAXSHIFT];
+        for (int k = 0; k < n; k++) all[k] = k;
+        double rr[STAG_MAXSHIFT];
+        if ((st = batched_true_residuals(ctx, mass, shifts, all, n, src, X, R, rr, s))) return st;
+        info->matvecs += n;
+        const double bb = ctx->hscal[1];
+        int ks[STAG_MAXSHIFT], nk = 0;
+        for (int k = 0; k < n; k++)
+            if (bb > 0.0 && rr[k] > tol * tol * bb) ks[nk++] = k;
+        if (nk > 0) {
+            int its[STAG_MAXSHIFT] = {0}, rel = 0, mv = 0;
+            // the refinement always uses FP32 links: BF16's ~4e-3 operator error times
+            // the condition number of the light shifts exceeds one, and an inner
+            // iteration that far from the true operator does not converge
+            st = refine_batched(ctx, LP32, mass, shifts, ks, nk, src, bb, X, R, tol, maxit, rr, its, &rel, &mv, s);
+            if (st) return st;
+            for (int i = 0; i < nk; i++) info->refine_iters[ks[i]] = its[ks[i]];
+            info->reliable_updates += rel;
+            info->matvecs += mv;
+        }
+        int status = STAG_OK;
+        for (int k = 0; k < n; k++) {
+            info->true_resid[k] = (bb > 0.0) ? sqrt(rr[k] / bb) : 0.0;
+            if (!isfinite(info->true_resid[k])) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite solution");
+            if (rr[k] > tol * tol * bb * 1.0000001) status = STAG_ERR_NOCONV;
+        }
+        if (sols) {
+            for (int k = 0; k < n; k++)
+                if (sols[k] && sols[k] != X + k * n3)
+                    STAG_CUDA(ctx, cudaMemcpyAsync(sols[k], X + k * n3, vb64, cudaMemcpyDeviceToDevice, s));
+        }
+        info->status = status;
+        if (status) return stag_fail(ctx, status, "solver did not reach tolerance %.3g", tol);
+        return STAG_OK;
+    }
+
     // FP64 true residual of every shift; mixed mode refines the ones above tol
     double2* w64 = (double2*)ws_get(ctx, WS_W64, vb64);
     double2* t64 = (double2*)ws_get(ctx, WS_T64, vb64);
     if ((st = blas_dot_re(ctx, STAG_PREC_F64, src, src, ctx->dscal + 1, s))) return st;
     for (int k = 0; k < n; k++) {
-        if ((st = true_residual2(ctx, mass * mass + shifts[k], src, X + k * n3, w64, t64, nullptr, nullptr,
+        if ((st = true_residual2(ctx, check_prec, mass * mass + shifts[k], src, X + k * n3, w64, t64, nullptr, nullptr,
                                  ctx->dscal + 100 + k, s)))
             return st;
     }

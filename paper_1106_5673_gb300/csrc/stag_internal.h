@@ -28,6 +28,7 @@ enum WsSlot {
     WS_FX, WS_FY,                         // force: X_k (even), Y_k (odd), FP64
     WS_PHI, WS_RGAUSS, WS_RAT,            // trajectory: pseudofermions, R, r(M) phi
     WS_FORCE,                             // force accumulator [4][2][8][Vh] doubles
+    WS_BR, WS_BW, WS_BT, WS_BPART,        // batched refinement: residuals, M p, odd temp, partials
     WS_NSLOTS
 };
 
@@ -50,12 +51,26 @@ struct CGState {
     int iter, maxit, live, stop_next, want_reliable, nonfinite;
 };
 
+// Device-resident state of the batched refinement: one CG per right-hand side
+// (shift), all advanced by the same kernels.  RHS j uses vector slot j.
+struct BCGState {
+    double rr[STAG_MAXSHIFT], rr_prev[STAG_MAXSHIFT], rr_max[STAG_MAXSHIFT];
+    double alpha[STAG_MAXSHIFT], beta[STAG_MAXSHIFT], c0[STAG_MAXSHIFT];
+    double tol2bb, delta2;
+    int act[STAG_MAXSHIFT];       // active RHS slots, compacted; n_act of them
+    int uact[STAG_MAXSHIFT];      // slots updated by the current iteration (fused path)
+    int want_rel[STAG_MAXSHIFT];  // per slot: reliable update requested
+    int iter[STAG_MAXSHIFT];      // per slot: iterations done
+    int n_act, n_uact, maxit, live, stop_next, nonfinite;
+};
+
 struct stag_ctx {
     Geom g;
     int device;
     char err[512];
     double2* U64;       // [4][2][6][Vh]
     float4* U32;        // [4][2][3][Vh]
+    float4* U32lo;      // [4][2][3][Vh]  fl32(U64 - U32): low words of the float-float links
     uint2* U16;         // [4][2][3][Vh]
     double2* U64_save;  // copy kept for the Metropolis reject
     double* mom;        // [4][2][8][Vh]
@@ -68,6 +83,8 @@ struct stag_ctx {
     MSState* ms_host;   // pinned host mirror
     CGState* cg;        // device single-shift state
     CGState* cg_host;   // pinned host mirror
+    BCGState* bcg;      // device batched-refinement state
+    BCGState* bcg_host; // pinned host mirror
     void* ws[WS_NSLOTS];
     size_t ws_bytes[WS_NSLOTS];
     size_t fixed_bytes;
@@ -129,6 +146,13 @@ int blas_rational_combine(stag_ctx* ctx, double a0, const double* a, int n, cons
 int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src,
                      double2* const* sols, double tol, int maxit, int mode, stag_solve_info* info,
                      cudaStream_t s);
+
+// ---------------------------------------------------------------- refine.cu
+int batched_true_residuals(stag_ctx* ctx, double mass, const double* shifts, const int* ks, int nk, const double2* b,
+                           const double2* X, float2* R, double* rr_out, cudaStream_t s);
+int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, const int* ks, int nk, const double2* b,
+                   double bb, double2* X, float2* R, double tol, int maxit, double* rr, int* iters, int* reliable,
+                   int* matvecs, cudaStream_t s);
 
 // ---------------------------------------------------------------- force.cu
 // F (internal) (+)= fermion force for sum_k a_k X_k, Y_k = D_oe X_k; X contiguous FP64

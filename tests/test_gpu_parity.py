@@ -90,6 +90,38 @@ def test_M_ee_f64_and_f32(S, dims):
     assert rel(host(out32), ref) < 5e-6
 
 
+@pytest.mark.parametrize("dims", SHAPES)
+def test_float_float_operator_is_fp64_accurate(S, dims):
+    """The float-float hop (FP32 pipes, hi/lo pairs) matches the FP64 oracle to
+    1e-12 relative: it is an FP64-accurate operator, not an FP32 one."""
+    U = synth.haar_links(dims, 21)
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    x = synth.gaussian_vector(dims, 22)
+    out = L.vector()
+    L.apply_doe(dev(x), out, S.PREC_F64FF)
+    assert rel(host(out), O.dslash(dims, U, 1, x)) < 1e-12
+    out = L.vector()
+    L.apply_M(0.01, dev(x), out, S.PREC_F64FF)
+    assert rel(host(out), O.apply_M(dims, U, 0.01, x)) < 1e-12
+
+
+def test_multishift_float_float_mode(S):
+    dims, m = (8, 8, 8, 8), 0.05
+    U = synth.haar_links(dims, 23)
+    b = synth.gaussian_vector(dims, 24)
+    shifts = synth.log_shifts(8, 1e-4, 1.0)
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    tol = 1e-10
+    sols, info = L.multishift_solve(m, shifts, dev(b), tol=tol, mode=S.SOLVE_F64FF)
+    xo, its, tot, st = O.multishift(dims, U, m, shifts, b, tol=tol)
+    assert info.status == 0 and abs(info.iters - tot) <= 3
+    for k in range(len(shifts)):
+        assert info.true_resid[k] <= tol
+        assert rel(host(sols[k]), xo[k]) < 1e-8
+
+
 def test_M_ee_full_size_32x32x32x8(S):
     """The operator at the size of the 32^3x8 trajectory, checked in full."""
     dims = (32, 32, 32, 8)
