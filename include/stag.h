@@ -167,6 +167,25 @@ int stag_apply_doe(stag_ctx *ctx, const void *in_even, void *out_odd, int prec, 
 int stag_apply_M(stag_ctx *ctx, double mass, const void *in_even, void *out_even, int prec,
                  void *stream);
 
+/* Allocation-free M_ee.  The paper has no counterpart: this serves callers
+ * that must not allocate device memory when they apply the operator -- code
+ * inside a framework that owns the device's memory pool, where a cudaMalloc
+ * behind its back breaks its accounting or its cap, and latency-critical
+ * loops, where cudaMalloc's implicit device synchronisation stalls every
+ * stream.  Needs no context: `links` is the gauge field on the device in the
+ * canonical layout, in_even/out_even FP64 device vectors (canonical, even
+ * sites), all owned by the caller; out = m^2 in - D_eo D_oe in in FP64.
+ * The odd-site intermediate lives in a fixed array inside the library of
+ * 2^17 sites (6 MiB), resident on every device that loads the library until
+ * exit; lattices with V/2 > 2^17 (larger than 32^3 x 8) are rejected with
+ * STAG_ERR_ARG.  The first call on a device looks up the array's address
+ * (set-up); make that first call before any stream capture.  All calls share
+ * the array: calls whose kernels overlap on the GPU race.  Returns STAG_OK,
+ * STAG_ERR_ARG (bad sizes or pointers) or STAG_ERR_CUDA; there is no error
+ * string, since there is no context.  Asynchronous on `stream`. */
+int stag_apply_M_noalloc(const int dims[4], const double *links, double mass, const double *in_even,
+                         double *out_even, void *stream);
+
 /* ---------------- solvers (Sec. 4.3, Eq. (13)) ---------------- */
 
 /* Solves (M_ee + shifts[k]) x_k = src for k < n (1 <= n <= STAG_MAXSHIFT,

@@ -113,6 +113,7 @@ _SIGS = {
     "stag_md_trajectory": (C.c_int, [_vp, C.POINTER(Params), C.POINTER(TrajInfo), _vp]),
     "stag_remez": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(Rational),
                              _dp]),
+    "stag_apply_M_noalloc": (C.c_int, [C.POINTER(C.c_int), _vp, C.c_double, _vp, _vp, _vp]),
 }
 
 
@@ -145,6 +146,15 @@ def remez(power, lo, hi, degree):
         raise StagError(st, "remez failed for p=%g on [%g, %g] degree %d" % (power, lo, hi, degree))
     a0, a, b = r.as_tuple()
     return a0, a, b, err.value
+
+
+def apply_M_noalloc(dims, links, mass, x_even, out_even):
+    """out = M_ee x through the allocation-free entry point: `links` is the
+    canonical gauge field as a complex128 CUDA tensor [4, V, 3, 3]; nothing is
+    allocated on the device by the call.  Returns the status code."""
+    d = (C.c_int * 4)(*[int(v) for v in dims])
+    return lib().stag_apply_M_noalloc(d, _ptr(links), float(mass), _ptr(x_even), _ptr(out_even),
+                                      _stream())
 
 
 def _torch():
