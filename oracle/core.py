@@ -55,7 +55,7 @@ class Params(C.Structure):
                 ("lam", C.c_double), ("tol_md", C.c_double), ("tol_metro", C.c_double),
                 ("nsteps", C.c_int), ("integrator", C.c_int), ("npf", C.c_int),
                 ("maxit", C.c_int), ("seed", C.c_uint32), ("traj", C.c_uint32),
-                ("hb", Rational), ("act", Rational), ("force", Rational)]
+                ("hb", Rational), ("act", Rational), ("force", Rational), ("ngauge", C.c_int)]
 
 
 class TrajInfo(C.Structure):
@@ -254,9 +254,11 @@ def update_links(dims, U, w, eps):
 
 
 def make_params(beta, mass, tau, nsteps, integrator, hb, act, force, npf=1, tol_md=1e-10,
-                tol_metro=1e-10, seed=0, traj=0, lam=0.1931833275037836, maxit=100000):
-    """hb/act/force are (a0, a, b) tuples."""
+                tol_metro=1e-10, seed=0, traj=0, lam=0.1931833275037836, maxit=100000, ngauge=0):
+    """hb/act/force are (a0, a, b) tuples; ngauge > 0 selects the multi-step
+    scheme with ngauge gauge steps per fermion-scheme position update."""
     p = Params()
+    p.ngauge = ngauge
     p.beta, p.mass, p.tau, p.lam = beta, mass, tau, lam
     p.tol_md, p.tol_metro = tol_md, tol_metro
     p.nsteps, p.integrator, p.npf, p.maxit = nsteps, integrator, npf, maxit

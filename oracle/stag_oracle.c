@@ -780,6 +780,23 @@ void or_update_momenta(const int dims[4], double *w, const double *F, double eps
 /* Molecular dynamics and the trajectory (Sec. 2.1)                          */
 /* ------------------------------------------------------------------------ */
 
+/* fermion part of dP/dtau: sum over pseudofermions of the fermion force */
+static int fermion_force_all(const int dims[4], const double *U, const double *phi, const or_params *p,
+                             double *F, double *Ff, long *cg_iters)
+{
+    long V = or_volume(dims), N = 6 * (V / 2);
+    int st = 0;
+    for (long i = 0; i < 32 * V; i++) F[i] = 0.0;
+    for (int pf = 0; pf < p->npf; pf++) {
+        int it = 0;
+        st |= or_fermion_force(dims, U, p->mass, &p->force, phi + pf * N, p->tol_md, p->maxit, Ff,
+                               &it);
+        *cg_iters += it;
+        for (long i = 0; i < 32 * V; i++) F[i] += Ff[i];
+    }
+    return st;
+}
+
 /* total force dP/dtau = gauge force + sum over pseudofermions of the fermion force */
 static int total_force(const int dims[4], const double *U, const double *phi, const or_params *p,
                        double *F, double *Ff, long *cg_iters)
@@ -797,44 +814,85 @@ static int total_force(const int dims[4], const double *U, const double *phi, co
     return st;
 }
 
+/* Inner scheme of the multi-step integrator: ngauge steps of size d = h/ngauge
+ * of the same scheme (leapfrog or 2MN) moving U and P with the gauge force
+ * only, written out step by step without merging the momentum updates. */
+static void gauge_substeps(const int dims[4], double *U, double *w, const or_params *p, double h,
+                           double *Fg)
+{
+    double d = h / p->ngauge, lam = p->lambda;
+    for (int j = 0; j < p->ngauge; j++) {
+        if (p->integrator == 0) {
+            or_gauge_force(dims, U, p->beta, Fg);
+            or_update_momenta(dims, w, Fg, 0.5 * d);
+            or_update_links(dims, U, w, d);
+            or_gauge_force(dims, U, p->beta, Fg);
+            or_update_momenta(dims, w, Fg, 0.5 * d);
+        } else {
+            or_gauge_force(dims, U, p->beta, Fg);
+            or_update_momenta(dims, w, Fg, lam * d);
+            or_update_links(dims, U, w, 0.5 * d);
+            or_gauge_force(dims, U, p->beta, Fg);
+            or_update_momenta(dims, w, Fg, (1.0 - 2.0 * lam) * d);
+            or_update_links(dims, U, w, 0.5 * d);
+            or_gauge_force(dims, U, p->beta, Fg);
+            or_update_momenta(dims, w, Fg, lam * d);
+        }
+    }
+}
+
 /* Integrate Hamilton's equations over tau with nsteps steps of size
  * eps = tau/nsteps.  Leapfrog (PQP): P(eps/2) Q(eps) P(eps/2) per step.
  * Omelyan second-order minimum norm (2MN):
  * P(l eps) Q(eps/2) P((1-2l) eps) Q(eps/2) P(l eps) per step.
- * Adjacent momentum half-steps of consecutive steps are merged (same force). */
+ * Adjacent momentum half-steps of consecutive steps are merged (same force).
+ * Multi-step scheme (ngauge > 0; Sec. 2.1's "multi-step integrator, with
+ * action divided in gauge and fermion part", after Sexton and Weingarten):
+ * the scheme above moves P with the fermion force only, and each of its
+ * position updates Q(h) becomes ngauge inner steps over time h that move U
+ * and P with the gauge force (gauge_substeps). */
 int or_md_integrate(const int dims[4], double *U, double *w, const double *phi,
                     const or_params *p, long *cg_iters, int *n_force)
 {
     long V = or_volume(dims);
     double *F = malloc(sizeof(double) * 32 * V), *Ff = malloc(sizeof(double) * 32 * V);
+    double *Fg = malloc(sizeof(double) * 32 * V);
     double eps = p->tau / p->nsteps;
     long it = 0;
     int nf = 0, st = 0;
+    int multi = p->ngauge > 0;
+#define OR_FORCE() (multi ? fermion_force_all(dims, U, phi, p, F, Ff, &it) \
+                          : total_force(dims, U, phi, p, F, Ff, &it))
+#define OR_MOVE(h) do { if (multi) gauge_substeps(dims, U, w, p, (h), Fg); \
+                        else or_update_links(dims, U, w, (h)); } while (0)
     if (p->integrator == 0) {
-        st |= total_force(dims, U, phi, p, F, Ff, &it); nf++;
+        st |= OR_FORCE(); nf++;
         or_update_momenta(dims, w, F, 0.5 * eps);
         for (int s = 0; s < p->nsteps; s++) {
-            or_update_links(dims, U, w, eps);
-            st |= total_force(dims, U, phi, p, F, Ff, &it); nf++;
+            OR_MOVE(eps);
+            st |= OR_FORCE(); nf++;
             or_update_momenta(dims, w, F, (s == p->nsteps - 1) ? 0.5 * eps : eps);
         }
     } else {
         double lam = p->lambda;
-        st |= total_force(dims, U, phi, p, F, Ff, &it); nf++;
+        st |= OR_FORCE(); nf++;
         or_update_momenta(dims, w, F, lam * eps);
         for (int s = 0; s < p->nsteps; s++) {
-            or_update_links(dims, U, w, 0.5 * eps);
-            st |= total_force(dims, U, phi, p, F, Ff, &it); nf++;
+            OR_MOVE(0.5 * eps);
+            st |= OR_FORCE(); nf++;
             or_update_momenta(dims, w, F, (1.0 - 2.0 * lam) * eps);
-            or_update_links(dims, U, w, 0.5 * eps);
-            st |= total_force(dims, U, phi, p, F, Ff, &it); nf++;
+            OR_MOVE(0.5 * eps);
+            st |= OR_FORCE(); nf++;
             or_update_momenta(dims, w, F, (s == p->nsteps - 1) ? lam * eps : 2.0 * lam * eps);
         }
     }
+#undef OR_FORCE
+#undef OR_MOVE
     if (cg_iters) *cg_iters += it;
     if (n_force) *n_force += nf;
     free(F);
     free(Ff);
+    free(Fg);
     return st;
 }
 

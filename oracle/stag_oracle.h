@@ -38,6 +38,8 @@ typedef struct {
     int maxit;       /* CG iteration cap                              */
     uint32_t seed, traj;
     or_rational hb, act, force;  /* r_{1/4}, r_{-1/2} (Metropolis), r_{-1/2} (MD) */
+    int ngauge;      /* 0: one time scale; n > 0: multi-step scheme, n gauge steps
+                        per position update of the fermion scheme              */
 } or_params;
 
 typedef struct {

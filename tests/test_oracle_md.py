@@ -184,3 +184,60 @@ def test_heatbath_start_action(rationals):
     RR = np.vdot(R, R).real
     bound = (2 * h["err"] + r["err"]) * 1.01 + 1e-12
     assert abs(S / RR - 1) < bound
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_multistep_without_fermions_is_fine_gauge_integrator(rationals, integrator):
+    """npf = 0: the fermion scheme's momentum updates vanish and the multi-step
+    integrator is the single-scale one with nsteps * ngauge (leapfrog) or
+    nsteps * 2 ngauge (2MN) gauge steps."""
+    dims = (2, 2, 2, 4)
+    U = synth.near_unit_links(dims, 0.3, 30)
+    W = synth.gaussian_momenta(dims, 31)
+    phi = np.zeros((1, 3 * synth.volume(dims) // 2), complex)
+    ng, ns = 3, 2
+    pm = _params(rationals, integrator=integrator, nsteps=ns, ngauge=ng, npf=0)
+    fine = ns * ng * (1 if integrator == 0 else 2)
+    ps = _params(rationals, integrator=integrator, nsteps=fine, npf=0)
+    U1, W1, _, _, st1 = O.md_integrate(dims, U, W, phi, pm)
+    U2, W2, _, _, st2 = O.md_integrate(dims, U, W, phi, ps)
+    assert st1 == 0 and st2 == 0
+    assert np.abs(U1 - U).max() > 1e-2
+    assert np.abs(U1 - U2).max() < 1e-12 and np.abs(W1 - W2).max() < 1e-11
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_multistep_at_zero_beta_is_single_scale(rationals, integrator):
+    """beta = 0: the inner steps only move U, ngauge times by h/ngauge, which
+    composes to one move by h; the result is the single-scale integrator."""
+    dims = (2, 2, 2, 4)
+    U = synth.near_unit_links(dims, 0.3, 32)
+    W = synth.gaussian_momenta(dims, 33)
+    phi = synth.gaussian_vector(dims, 34)[None]
+    pm = _params(rationals, integrator=integrator, nsteps=3, ngauge=4, beta=0.0)
+    ps = _params(rationals, integrator=integrator, nsteps=3, beta=0.0)
+    U1, W1, _, nf1, _ = O.md_integrate(dims, U, W, phi, pm)
+    U2, W2, _, nf2, _ = O.md_integrate(dims, U, W, phi, ps)
+    assert nf1 == nf2
+    assert np.abs(U1 - U2).max() < 1e-12 and np.abs(W1 - W2).max() < 1e-11
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_multistep_reversible_and_second_order(rationals, integrator):
+    dims = (2, 2, 2, 4)
+    U = synth.near_unit_links(dims, 0.3, 35)
+    W = synth.gaussian_momenta(dims, 36)
+    phi = synth.gaussian_vector(dims, 37)[None]
+    p = _params(rationals, integrator=integrator, nsteps=3, ngauge=2)
+    U1, W1, _, _, st = O.md_integrate(dims, U, W, phi, p)
+    U2, W2, _, _, _ = O.md_integrate(dims, U1, -W1, phi, p)
+    assert st == 0
+    assert np.abs(U - U2).max() < 1e-12 and np.abs(W + W2).max() < 1e-11
+    dH = []
+    for n in (4, 8, 16):
+        p = _params(rationals, integrator=integrator, nsteps=n, ngauge=2)
+        H0 = O.hamiltonian(dims, U, W, phi, p)
+        U1, W1, _, _, _ = O.md_integrate(dims, U, W, phi, p)
+        dH.append(abs(O.hamiltonian(dims, U1, W1, phi, p) - H0))
+    r1, r2 = dH[0] / dH[1], dH[1] / dH[2]
+    assert 3.0 < r1 < 5.5 and 3.5 < r2 < 4.5, dH
