@@ -67,13 +67,26 @@ enum { STAG_PREC_F64 = 0, STAG_PREC_F32 = 1, STAG_PREC_BF16 = 2, STAG_PREC_F64FF
  *              reliable updates); every shift checked FP64-accurately;
  *  MIXED_BF16  as MIXED with BF16 links in the FP32 kernels;
  *  F64FF       FP64 vectors and recurrences with the float-float operator
- *              (STAG_PREC_F64FF) in place of native FP64 arithmetic. */
-enum { STAG_SOLVE_F64 = 0, STAG_SOLVE_MIXED = 1, STAG_SOLVE_MIXED_BF16 = 2, STAG_SOLVE_F64FF = 3 };
+ *              (STAG_PREC_F64FF) in place of native FP64 arithmetic;
+ *  LEARNED     the lightest shift by flexible CG preconditioned with the
+ *              network attached by stag_ctx_set_net, the other shifts by the
+ *              MIXED solver (whose shifted CG is then based at the second
+ *              lightest shift); if the flexible CG misses tol within its cap
+ *              (STAG_FCG_MAXIT, default 2000 iterations) the MIXED solver is
+ *              re-run over all shifts.  Every shift checked FP64-accurately. */
+enum {
+    STAG_SOLVE_F64 = 0,
+    STAG_SOLVE_MIXED = 1,
+    STAG_SOLVE_MIXED_BF16 = 2,
+    STAG_SOLVE_F64FF = 3,
+    STAG_SOLVE_LEARNED = 4
+};
 
 enum { STAG_INT_LEAPFROG = 0, STAG_INT_OMELYAN = 1 };
 
 #define STAG_MAXSHIFT 32
 #define STAG_MAXPF 8
+#define STAG_MAXRHS 8 /* systems of one batched multi-shift solve */
 
 typedef struct stag_ctx stag_ctx;
 
@@ -101,7 +114,7 @@ typedef struct {
     int nsteps;                 /* MD steps of size tau/nsteps                      */
     int integrator;             /* STAG_INT_LEAPFROG or STAG_INT_OMELYAN           */
     double lambda;              /* Omelyan 2MN parameter (0.1931833275037836)       */
-    int npf;                    /* pseudofermions, 1..STAG_MAXPF                    */
+    int npf;                    /* pseudofermions, 0..STAG_MAXPF (0: pure gauge)    */
     stag_rational hb;           /* r ~ x^{+1/(4 npf)}  heatbath                     */
     stag_rational act;          /* r ~ x^{-1/(2 npf)}  action (Metropolis)          */
     stag_rational force;        /* r ~ x^{-1/(2 npf)}  molecular dynamics           */
@@ -111,6 +124,16 @@ typedef struct {
     int maxit;                  /* iteration cap of every solve                     */
     uint32_t seed, traj;        /* Philox key (seed, traj)                          */
     int use_graphs;             /* capture the MD loop's force/update steps         */
+    int ngauge;                 /* 0: one time scale.  n > 0: multi-step scheme
+                                   (Sec. 2.1, Sexton-Weingarten): the integrator
+                                   moves P with the fermion force only, and each
+                                   of its position updates Q(h) is n inner steps
+                                   of the same scheme over h with the gauge force
+                                   (step ratio dtau_f/dtau_g = n for leapfrog,
+                                   2n for Omelyan)                                  */
+    int no_metropolis;          /* 1: accept every trajectory (molecular-dynamics
+                                   thermalisation of a start configuration only;
+                                   not an exact algorithm).  0: Metropolis test   */
 } stag_params;
 
 typedef struct {
@@ -136,6 +159,13 @@ int stag_ctx_device_bytes(const stag_ctx *ctx, size_t *bytes);
 /* Number of CUDA kernels the context has launched so far (kernels inside
  * captured graphs counted one by one); for accounting in benchmarks. */
 int stag_ctx_launch_count(const stag_ctx *ctx, long long *n);
+/* Autotuner: times the hop kernels for 64, 128 and 256 threads per block for
+ * each link precision (FP64, FP32, BF16, float-float; CUDA events after
+ * warm-up) on the loaded gauge field and keeps the fastest for this context;
+ * tpb_out (nullable, 4 ints) receives the choice.  The first solve on a
+ * context runs it automatically unless the environment sets STAG_AUTOTUNE=0.
+ * Synchronises. */
+int stag_autotune(stag_ctx *ctx, int tpb_out[4], void *stream);
 
 /* ---------------- fields ---------------- */
 
@@ -202,6 +232,18 @@ int stag_multishift_solve(stag_ctx *ctx, double mass, int n, const double *shift
                           const double *src, double *const *sols, double tol, int maxit,
                           int mode, stag_solve_info *info, void *stream);
 
+/* Batched form: solves (M_ee + shifts[k]) x_{r,k} = srcs[r] for nsys systems
+ * (1 <= nsys <= STAG_MAXRHS, e.g. the pseudofermions of one force
+ * evaluation) and the same n shifts, advancing all systems together: the hop
+ * kernels load each link once for a group of systems.  Each system stops on
+ * its own; mixed modes refine every (system, shift) above tolerance in
+ * batches of STAG_MAXSHIFT.  sols[r*n + k] (nullable entries; sols itself
+ * nullable) receive the FP64 solutions; infos (nullable) holds nsys entries.
+ * Synchronises.  Errors as stag_multishift_solve. */
+int stag_multishift_solve_multi(stag_ctx *ctx, double mass, int nsys, int n, const double *shifts,
+                                const double *const *srcs, double *const *sols, double tol, int maxit,
+                                int mode, stag_solve_info *infos, void *stream);
+
 /* out = r(M_ee) src = a0 src + sum_k a_k (M_ee + b_k)^{-1} src (RHMC, Sec. 2.1).
  * FP64 device vectors; out may not alias src.  Synchronises. */
 int stag_rational_apply(stag_ctx *ctx, double mass, const stag_rational *r, const double *src,
@@ -247,6 +289,50 @@ int stag_kinetic(stag_ctx *ctx, double *out, void *stream);
  * integrator, H1, Metropolis with u from Philox counter (3,0,0,0); on
  * rejection the gauge field is restored.  Synchronises. */
 int stag_md_trajectory(stag_ctx *ctx, const stag_params *p, stag_traj_info *out, void *stream);
+
+/* ---------------- learned preconditioner (no counterpart in the paper) ------
+ * A gauge-covariant network K = restrict_even L3 L2 L1 embed_even with
+ * channels 1 -> 8 -> 8 -> 1; each layer is a parallel-transport convolution
+ *   (L phi)_o(n) = sum_i sum_t w[o][i][t] (T_t phi_i)(n),  t = 0..8:
+ *   T_0 phi = phi(n), T_{1+mu} phi = U_mu(n) phi(n+mu),
+ *   T_{5+mu} phi = U_mu(n-mu)^dag phi(n-mu),
+ * so K commutes with gauge transformations.  Weights: complex, layout
+ * [c_out][c_in][9] (re, im floats), BF16 in the forward pass, FP32 master and
+ * FP32 arithmetic.  Trained with Adam on (source, solution) pairs to
+ * minimise mean |K b - x|^2 / |x|^2; gradients are dloss/dRe w + i dloss/dIm w. */
+typedef struct stag_net stag_net;
+
+/* Creates a network bound to ctx (its gauge field), weights initialised near
+ * the identity from `seed`.  Synchronises. */
+int stag_net_create(stag_ctx *ctx, unsigned seed, stag_net **out);
+/* Frees the network (detaching it from its context if attached). */
+int stag_net_destroy(stag_net *net);
+/* Attaches net (created on ctx) as the preconditioner of STAG_SOLVE_LEARNED;
+ * NULL detaches.  The network is borrowed, not owned. */
+int stag_ctx_set_net(stag_ctx *ctx, stag_net *net);
+/* Complex weights of layer 0..2 (72, 576, 72). */
+int stag_net_nweights(const stag_net *net, int layer, int *n);
+/* Host copies of the FP32 master weights / of the last gradients (2 floats per
+ * complex weight); set replaces the weights (and their BF16 copy). */
+int stag_net_get_weights(stag_net *net, int layer, float *host);
+int stag_net_set_weights(stag_net *net, int layer, const float *host);
+int stag_net_get_grads(stag_net *net, int layer, float *host);
+/* out_even = K in_even (FP64 device vectors). */
+int stag_net_apply(stag_net *net, const double *in_even, double *out_even, void *stream);
+/* Loss of the pairs (srcs[j], sols[j]) and its weight gradients (read them with
+ * stag_net_get_grads).  Synchronises. */
+int stag_net_loss_grad(stag_net *net, int npairs, const double *const *srcs, const double *const *sols,
+                       double *loss, void *stream);
+/* `epochs` passes of Adam (learning rate lr) over minibatches of `batch`
+ * pairs; *loss receives the mean loss of the last epoch.  Synchronises. */
+int stag_net_train(stag_net *net, int npairs, const double *const *srcs, const double *const *sols, int epochs,
+                   int batch, double lr, double *loss, void *stream);
+/* Solves (M_ee + shift) x = src (FP64 device vectors) by flexible CG with the
+ * network as right preconditioner (net == NULL: plain CG), FP64 vectors and
+ * the FP64-accurate float-float operator; stops at |r| <= tol |src| and
+ * reports the true residual in info->true_resid[0].  Synchronises. */
+int stag_fcg_solve(stag_ctx *ctx, stag_net *net, double mass, double shift, const double *src, double *sol,
+                   double tol, int maxit, stag_solve_info *info, void *stream);
 
 /* ---------------- host helper ---------------- */
 

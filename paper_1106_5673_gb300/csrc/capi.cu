@@ -31,6 +31,7 @@ static void clear_graphs(stag_ctx* ctx) {
     for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
     ctx->graphs.clear();
 }
+void ctx_clear_graphs(stag_ctx* ctx) { clear_graphs(ctx); }
 
 // Returns a device buffer of at least `bytes` for `slot`; grows it if needed
 // (which invalidates captured graphs, since they hold raw pointers).
@@ -96,9 +97,14 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     const size_t Vh = ctx->g.Vh;
-    int maxb = (int)(4 * (Vh / 128 + 2));  // four partial sums per hop block
+    int maxb = (int)(4 * (Vh / 64 + 2));  // four partial sums per hop block of >= 64 threads
     if (maxb < (int)(V / 256 + 2)) maxb = (int)(V / 256 + 2);
     if (maxb < 16 * ctx->num_sms) maxb = 16 * ctx->num_sms;
+    // two-level reductions: one counter and 4 * STAG_MAXSHIFT group sums per
+    // group of STAG_RED_GROUP blocks of >= 64 threads
+    const size_t ngroups = (Vh / 64 + 2) / STAG_RED_GROUP + 2;
+    const size_t counter_bytes = sizeof(unsigned int) * (64 + ngroups);
+    ctx->counter_bytes = counter_bytes;
     struct { void** p; size_t bytes; } allocs[] = {
         {(void**)&ctx->U64, sizeof(double2) * 48 * Vh},
         {(void**)&ctx->U32, sizeof(float4) * 24 * Vh},
@@ -107,11 +113,14 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
         {(void**)&ctx->U64_save, sizeof(double2) * 48 * Vh},
         {(void**)&ctx->mom, sizeof(double) * 64 * Vh},
         {(void**)&ctx->partials, sizeof(double) * (size_t)maxb},
-        {(void**)&ctx->counter, 256},
+        {(void**)&ctx->counter, counter_bytes},
+        {(void**)&ctx->gpart, sizeof(double) * 4 * STAG_MAXSHIFT * ngroups},
         {(void**)&ctx->dscal, sizeof(double) * STAG_NSCAL},
         {(void**)&ctx->ms, sizeof(MSState)},
         {(void**)&ctx->cg, sizeof(CGState)},
         {(void**)&ctx->bcg, sizeof(BCGState)},
+        {(void**)&ctx->msm, sizeof(MSState) * STAG_MAXRHS},
+        {(void**)&ctx->mm_partials, sizeof(double) * 4 * STAG_MAXRHS * (Vh / 64 + 2)},
     };
     ctx->fixed_bytes = 0;
     for (auto& a : allocs) {
@@ -119,12 +128,13 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
         e = cudaMalloc(a.p, a.bytes);
         ctx->fixed_bytes += a.bytes;
     }
-    if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, 256);
+    if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, counter_bytes);
     if (e == cudaSuccess) e = cudaMemset(ctx->mom, 0, sizeof(double) * 64 * Vh);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->hscal, sizeof(double) * STAG_NSCAL);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->ms_host, sizeof(MSState));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->cg_host, sizeof(CGState));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->bcg_host, sizeof(BCGState));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->msm_host, sizeof(MSState) * STAG_MAXRHS);
     if (e != cudaSuccess) {
         st = (e == cudaErrorMemoryAllocation) ? STAG_ERR_OOM : STAG_ERR_CUDA;
         cudaGetLastError();
@@ -140,7 +150,8 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     cudaDeviceSynchronize();
     clear_graphs(ctx);
     void* ps[] = {ctx->U64, ctx->U32, ctx->U32lo, ctx->U16, ctx->U64_save, ctx->mom, ctx->partials,
-                  ctx->counter, ctx->dscal, ctx->ms, ctx->cg, ctx->bcg};
+                  ctx->counter, ctx->dscal, ctx->ms, ctx->cg, ctx->bcg, ctx->msm, ctx->mm_partials,
+                  ctx->gpart};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int i = 0; i < WS_NSLOTS; i++)
@@ -149,6 +160,7 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     if (ctx->ms_host) cudaFreeHost(ctx->ms_host);
     if (ctx->cg_host) cudaFreeHost(ctx->cg_host);
     if (ctx->bcg_host) cudaFreeHost(ctx->bcg_host);
+    if (ctx->msm_host) cudaFreeHost(ctx->msm_host);
     delete ctx;
     return STAG_OK;
 }
@@ -158,6 +170,16 @@ const char* stag_last_error(const stag_ctx* ctx) { return ctx ? ctx->err : "null
 int stag_ctx_launch_count(const stag_ctx* ctx, long long* n) {
     if (!ctx || !n) return STAG_ERR_ARG;
     *n = ctx->nlaunch;
+    return STAG_OK;
+}
+
+int stag_autotune(stag_ctx* ctx, int tpb_out[4], void* stream) {
+    CHECK_CTX(ctx);
+    CHECK_GAUGE(ctx);
+    int st = autotune_hops(ctx, S(stream));
+    if (st) return st;
+    if (tpb_out)
+        for (int i = 0; i < 4; i++) tpb_out[i] = ctx->tpb[i];
     return STAG_OK;
 }
 
@@ -314,6 +336,34 @@ int stag_multishift_solve(stag_ctx* ctx, double mass, int n, const double* shift
                             S(stream));
 }
 
+int stag_multishift_solve_multi(stag_ctx* ctx, double mass, int nsys, int n, const double* shifts,
+                                const double* const* srcs, double* const* sols, double tol, int maxit, int mode,
+                                stag_solve_info* infos, void* stream) {
+    CHECK_CTX(ctx);
+    CHECK_GAUGE(ctx);
+    if (!shifts || !srcs) return stag_fail(ctx, STAG_ERR_ARG, "shifts or srcs is null");
+    if (nsys < 1 || nsys > STAG_MAXRHS || n < 1 || n > STAG_MAXSHIFT)
+        return stag_fail(ctx, STAG_ERR_ARG, "bad number of systems or shifts");
+    for (int r = 0; r < nsys; r++) CHECK_PTR(ctx, srcs[r]);
+    if (sols)
+        for (int i = 0; i < nsys * n; i++)
+            if (sols[i] && !aligned16(sols[i])) return stag_fail(ctx, STAG_ERR_ARG, "sols[%d] not aligned", i);
+    const long n3 = 3L * ctx->g.Vh;
+    double2* X = (double2*)ws_get(ctx, WS_MX, sizeof(double2) * n3 * STAG_MAXSHIFT * STAG_MAXRHS);
+    if (!X) return stag_fail(ctx, STAG_ERR_OOM, "solution workspace");
+    int st = multishift_solve_multi(ctx, mass, nsys, n, shifts, (const double2* const*)srcs, X, tol, maxit, mode,
+                                    infos, S(stream));
+    if (st) return st;
+    if (sols)
+        for (int r = 0; r < nsys; r++)
+            for (int k = 0; k < n; k++)
+                if (sols[r * n + k])
+                    STAG_CUDA(ctx, cudaMemcpyAsync(sols[r * n + k], X + ((size_t)r * STAG_MAXSHIFT + k) * n3,
+                                                   sizeof(double2) * n3, cudaMemcpyDeviceToDevice, S(stream)));
+    STAG_CUDA(ctx, cudaStreamSynchronize(S(stream)));
+    return STAG_OK;
+}
+
 int stag_rational_apply(stag_ctx* ctx, double mass, const stag_rational* r, const double* src, double* out,
                         double tol, int maxit, int mode, stag_solve_info* info, void* stream) {
     CHECK_CTX(ctx);
@@ -396,7 +446,8 @@ int stag_md_trajectory(stag_ctx* ctx, const stag_params* p, stag_traj_info* out,
     CHECK_CTX(ctx);
     CHECK_GAUGE(ctx);
     if (!p || !out) return stag_fail(ctx, STAG_ERR_ARG, "null params or output");
-    if (p->nsteps < 1 || !(p->tau > 0) || p->npf < 1 || p->npf > STAG_MAXPF || p->maxit < 1)
+    if (p->nsteps < 1 || !(p->tau > 0) || p->npf < 0 || p->npf > STAG_MAXPF || p->maxit < 1 || p->ngauge < 0 ||
+        p->ngauge > 1000)
         return stag_fail(ctx, STAG_ERR_ARG, "bad trajectory parameters");
     if (p->integrator != STAG_INT_LEAPFROG && p->integrator != STAG_INT_OMELYAN)
         return stag_fail(ctx, STAG_ERR_ARG, "unknown integrator");

@@ -10,7 +10,7 @@ static const int HOP_TPB = 128;
 // out = c * self - 1/2 hop(in)   (c = 0, self = null: out = -1/2 hop; sign
 // flipped by `scale`) -- generic epilogue: out = c * self + scale * hop2
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_hop(Geom g, const void* __restrict__ U,
+__global__ void __launch_bounds__(256) k_hop(Geom g, const void* __restrict__ U,
                                                  const typename VT<R>::T* __restrict__ in,
                                                  typename VT<R>::T* __restrict__ out, int par, R scale, R c,
                                                  const typename VT<R>::T* __restrict__ self) {
@@ -32,14 +32,15 @@ __global__ void __launch_bounds__(HOP_TPB) k_hop(Geom g, const void* __restrict_
 
 template <typename R, int LP>
 static void launch_hop(stag_ctx* ctx, const void* U, const void* in, void* out, int par, R scale, R c,
-                       const void* self, cudaStream_t s) {
-    k_hop<R, LP><<<nblocks(ctx->g.Vh, HOP_TPB), HOP_TPB, 0, s>>>(
-        ctx->g, U, (const typename VT<R>::T*)in, (typename VT<R>::T*)out, par, scale, c,
-        (const typename VT<R>::T*)self);
+                       const void* self, cudaStream_t s, int tpb = 0) {
+    if (tpb <= 0) tpb = hop_tpb(ctx, LP);
+    k_hop<R, LP><<<nblocks(ctx->g.Vh, tpb), tpb, 0, s>>>(ctx->g, U, (const typename VT<R>::T*)in,
+                                                         (typename VT<R>::T*)out, par, scale, c,
+                                                         (const typename VT<R>::T*)self);
 }
 
 // FP64-accurate hop in float-float arithmetic (FP64 vectors in and out)
-__global__ void __launch_bounds__(HOP_TPB) k_hop_ff(Geom g, const float4* __restrict__ Uhi,
+__global__ void __launch_bounds__(256) k_hop_ff(Geom g, const float4* __restrict__ Uhi,
                                                     const float4* __restrict__ Ulo, const double2* __restrict__ in,
                                                     double2* __restrict__ out, int par, double scale, double c,
                                                     const double2* __restrict__ self) {
@@ -62,10 +63,12 @@ __global__ void __launch_bounds__(HOP_TPB) k_hop_ff(Geom g, const float4* __rest
 static int hop_dispatch(stag_ctx* ctx, int prec, const void* in, void* out, int par, double scale, double c,
                         const void* self, cudaStream_t s) {
     switch (prec) {
-    case STAG_PREC_F64FF:
-        k_hop_ff<<<nblocks(ctx->g.Vh, HOP_TPB), HOP_TPB, 0, s>>>(ctx->g, ctx->U32, ctx->U32lo, (const double2*)in,
-                                                                (double2*)out, par, scale, c, (const double2*)self);
+    case STAG_PREC_F64FF: {
+        const int tpb = hop_tpb(ctx, LPFF);
+        k_hop_ff<<<nblocks(ctx->g.Vh, tpb), tpb, 0, s>>>(ctx->g, ctx->U32, ctx->U32lo, (const double2*)in,
+                                                         (double2*)out, par, scale, c, (const double2*)self);
         break;
+    }
     case STAG_PREC_F64: launch_hop<double, LP64>(ctx, ctx->U64, in, out, par, scale, c, self, s); break;
     case STAG_PREC_F32: launch_hop<float, LP32>(ctx, ctx->U32, in, out, par, (float)scale, (float)c, self, s); break;
     case STAG_PREC_BF16: launch_hop<float, LP16>(ctx, ctx->U16, in, out, par, (float)scale, (float)c, self, s); break;
@@ -86,12 +89,65 @@ int mee_apply(stag_ctx* ctx, int prec, double c, const void* in, void* out, void
     return hop_dispatch(ctx, prec, tmp, out, 0, -0.5, c, in, s);
 }
 
+// ---------------------------------------------------------------- autotuner
+// Times the D_oe hop of each link precision for 64, 128 and 256 threads per
+// block (CUDA events, after warm-up) and keeps the fastest per context: the
+// lattice is fixed per context, so one measurement serves all later solves.
+// Captured graphs are dropped, since they hold the old launch shapes.
+int autotune_hops(stag_ctx* ctx, cudaStream_t s) {
+    const long n3 = 3L * ctx->g.Vh;
+    double2* a = (double2*)ws_get(ctx, WS_TUNE, sizeof(double2) * n3 * 2);
+    if (!a) return stag_fail(ctx, STAG_ERR_OOM, "tuning buffers");
+    double2* b = a + n3;
+    STAG_CUDA(ctx, cudaMemsetAsync(a, 0, sizeof(double2) * n3 * 2, s));
+    cudaEvent_t e0, e1;
+    STAG_CUDA(ctx, cudaEventCreate(&e0));
+    STAG_CUDA(ctx, cudaEventCreate(&e1));
+    const int cand[3] = {64, 128, 256};
+    for (int lp = 0; lp < 4; lp++) {
+        float best = 1e30f;
+        int best_tpb = 128;
+        for (int c = 0; c < 3; c++) {
+            const int tpb = cand[c];
+            auto launch = [&]() {
+                switch (lp) {
+                case LP64: launch_hop<double, LP64>(ctx, ctx->U64, a, b, 1, 0.5, 0.0, nullptr, s, tpb); break;
+                case LP32: launch_hop<float, LP32>(ctx, ctx->U32, a, b, 1, 0.5f, 0.f, nullptr, s, tpb); break;
+                case LP16: launch_hop<float, LP16>(ctx, ctx->U16, a, b, 1, 0.5f, 0.f, nullptr, s, tpb); break;
+                default:
+                    k_hop_ff<<<nblocks(ctx->g.Vh, tpb), tpb, 0, s>>>(ctx->g, ctx->U32, ctx->U32lo, a, b, 1, 0.5, 0.0,
+                                                                     nullptr);
+                }
+            };
+            for (int w = 0; w < 2; w++) launch();
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 5; r++) launch();
+            cudaEventRecord(e1, s);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) return stag_cuda_check(ctx, e, "autotune");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_tpb = tpb;
+            }
+        }
+        ctx->tpb[lp] = best_tpb;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    STAG_LAUNCH_CHECK(ctx, "autotune");
+    ctx->tuned = 1;
+    ctx_clear_graphs(ctx);
+    return STAG_OK;
+}
+
 // ---------------------------------------------------------------- multi-RHS hop
 // One thread per (site, RHS block of NR vectors): each link is loaded once and
 // applied to NR right-hand sides (the force needs Y_k = D_oe X_k for every
 // shift k).  FP64 vectors, FP64 links.
 template <int NR>
-__global__ void __launch_bounds__(HOP_TPB) k_hop_multi64(Geom g, const double2* __restrict__ U,
+__global__ void __launch_bounds__(256) k_hop_multi64(Geom g, const double2* __restrict__ U,
                                                          const double2* __restrict__ in, double2* __restrict__ out,
                                                          int nrhs, int k0, int par) {
     const int h = blockIdx.x * blockDim.x + threadIdx.x;

@@ -252,12 +252,12 @@ STAG_D Vec3<R> hopL(const Geom& g, Links L, const typename VT<R>::T* __restrict_
 }
 
 // multi-RHS: acc[q] = 2 (D psi_q)(n) for the NR vectors psi_q = in + js[q] * stride,
-// q < nj; each link is loaded once for all of them (FP32 vectors)
-template <int LP, int NR>
-STAG_D void hop2_multi(const Geom& g, const void* __restrict__ U, const float2* __restrict__ in, size_t stride,
-                       const int* js, int nj, int h, int par, const Site& s, Vec3<float> acc[NR]) {
+// q < nj; each link is loaded once for all of them
+template <typename R, int LP, int NR>
+STAG_D void hop2_multiR(const Geom& g, const void* __restrict__ U, const typename VT<R>::T* __restrict__ in,
+                        size_t stride, const int* js, int nj, int h, int par, const Site& s, Vec3<R> acc[NR]) {
 #pragma unroll
-    for (int q = 0; q < NR; q++) acc[q] = vzero<float>();
+    for (int q = 0; q < NR; q++) acc[q] = vzero<R>();
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
         const int fl = nb_lex(g, s, mu, +1);
@@ -267,13 +267,20 @@ STAG_D void hop2_multi(const Geom& g, const void* __restrict__ U, const float2* 
             if (s.x[3] == g.L[3] - 1) sf = -sf;
             if (s.x[3] == 0) sb = -sb;
         }
-        const Mat3<float> uf = get_link<float, LP>(U, g, mu, par, h);
+        const Mat3<R> uf = get_link<R, LP>(U, g, mu, par, h);
 #pragma unroll
         for (int q = 0; q < NR; q++)
             if (q < nj) axpy_sign(acc[q], sf, mv(uf, load_vec(in + js[q] * stride, fl >> 1)));
-        const Mat3<float> ub = get_link<float, LP>(U, g, mu, 1 - par, bl >> 1);
+        const Mat3<R> ub = get_link<R, LP>(U, g, mu, 1 - par, bl >> 1);
 #pragma unroll
         for (int q = 0; q < NR; q++)
             if (q < nj) axpy_sign(acc[q], -sb, mdv(ub, load_vec(in + js[q] * stride, bl >> 1)));
     }
+}
+
+// FP32-vector form used by the batched refinement
+template <int LP, int NR>
+STAG_D void hop2_multi(const Geom& g, const void* __restrict__ U, const float2* __restrict__ in, size_t stride,
+                       const int* js, int nj, int h, int par, const Site& s, Vec3<float> acc[NR]) {
+    hop2_multiR<float, LP, NR>(g, U, in, stride, js, nj, h, par, s, acc);
 }

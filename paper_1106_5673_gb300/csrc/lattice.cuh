@@ -398,6 +398,58 @@ STAG_D void reduce_series(const double* partials, int nseries, int nb, double* o
     __syncthreads();
 }
 
+// Deterministic two-level grid reduction of nseries sums whose block partials
+// are at partials[s * gridDim.x + blockIdx.x] (blocks of every row y write the
+// series they own; unwritten entries are never read by a series' owner rows
+// only if the caller keeps them zero -- every caller writes all it reduces).
+// Level 1: the last block to finish among the gridDim.y x STAG_RED_GROUP
+// blocks of each column group sums that group's columns into
+// gpart[s * ngroups + group]; level 2: the last group to finish sums gpart.
+// One L2 round trip of 32 loads per series at each level instead of a serial
+// sweep over all partials.  Returns true in exactly one block, whose
+// out_shared[0..nseries) then holds the sums; counters[0] and
+// counters[1 + group] return to zero.
+#define STAG_RED_GROUP 32
+STAG_D bool grid_reduce_series(const double* partials, double* gpart, unsigned int* counters, int nseries,
+                               double* out_shared) {
+    __shared__ bool s_last;
+    const int nbx = gridDim.x, ngr = (nbx + STAG_RED_GROUP - 1) / STAG_RED_GROUP;
+    const int grp = blockIdx.x / STAG_RED_GROUP, g0 = grp * STAG_RED_GROUP;
+    const int gsz = (nbx - g0 < STAG_RED_GROUP) ? nbx - g0 : STAG_RED_GROUP;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(counters + 1 + grp, 1u);
+        s_last = (t == (unsigned int)(gsz * gridDim.y) - 1u);
+        if (s_last) counters[1 + grp] = 0;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int sidx = w; sidx < nseries; sidx += nw) {
+        double v = (lane < gsz) ? __ldcg(partials + (size_t)sidx * nbx + g0 + lane) : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) gpart[(size_t)sidx * ngr + grp] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int t = atomicAdd(counters, 1u);
+        s_last = (t == (unsigned int)ngr - 1u);
+        if (s_last) counters[0] = 0;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    for (int sidx = w; sidx < nseries; sidx += nw) {
+        double v = 0.0;
+        for (int i = lane; i < ngr; i += 32) v += __ldcg(gpart + (size_t)sidx * ngr + i);
+        v = warp_sum(v);
+        if (lane == 0) out_shared[sidx] = v;
+    }
+    __syncthreads();
+    return true;
+}
+
 // ---------------------------------------------------------------- shared helpers
 
 STAG_D Site site_from_lex(const Geom& g, int lex) {

@@ -43,7 +43,7 @@ STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
 }
 
 template <int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
+__global__ void __launch_bounds__(256) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
                                                  float2* __restrict__ T, size_t stride, const BCGState* st) {
     if (!st->live) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(HOP_TPB) k_b_A(Geom g, const void* __restrict_
 }
 
 template <int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_b_B(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
+__global__ void __launch_bounds__(256) k_b_B(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
                                                  const float2* __restrict__ P, float2* __restrict__ W, size_t stride,
                                                  BCGState* st, double* partials, unsigned int* counter) {
     if (!st->live) return;
@@ -166,7 +166,7 @@ __global__ void k_b_C(long n, size_t stride, float2* __restrict__ R, const float
                 st->rr[k] = rr_new;
                 if (!isfinite(rr_new)) bad = 1;
                 if (st->iter[k] >= st->maxit) capped = 1;
-                if (rr_new <= st->tol2bb) {
+                if (rr_new <= st->tol2bb[k]) {
                     st->want_rel[k] = 1;  // parked until the host checks it
                 } else {
                     st->act[keep++] = k;
@@ -206,10 +206,10 @@ __global__ void k_b_D(long n, size_t stride, const float2* __restrict__ R, float
 // expansion, beta_k and the parking; CD applies r -= alpha w, x += alpha p and
 // (for right-hand sides still active) p = r + beta p.
 template <int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_b_B3(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
+__global__ void __launch_bounds__(256) k_b_B3(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
                                                   const float2* __restrict__ P, const float2* __restrict__ R,
                                                   float2* __restrict__ W, size_t stride, BCGState* st,
-                                                  double* partials, unsigned int* counter) {
+                                                  double* partials, double* gpart, unsigned int* counter) {
     if (!st->live) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     const int q0 = blockIdx.y * NR, nact = st->n_act;
@@ -260,9 +260,8 @@ __global__ void __launch_bounds__(HOP_TPB) k_b_B3(Geom g, const void* __restrict
             if (q < nj)
 #pragma unroll
                 for (int j = 0; j < 4; j++) partials[((size_t)(q0 + q) * 4 + j) * nbx + blockIdx.x] = flat[q * 4 + j];
-    if (last_block_n(counter, gridDim.x * gridDim.y)) {
-        __shared__ double s_sum[STAG_MAXSHIFT][4];
-        reduce_series(partials, nact * 4, (int)nbx, &s_sum[0][0]);
+    __shared__ double s_sum[STAG_MAXSHIFT][4];
+    if (grid_reduce_series(partials, gpart, counter, nact * 4, &s_sum[0][0])) {
         if (threadIdx.x == 0) {
             int keep = 0, bad = 0, capped = 0;
             for (int a = 0; a < nact; a++) {
@@ -279,7 +278,7 @@ __global__ void __launch_bounds__(HOP_TPB) k_b_B3(Geom g, const void* __restrict
                 st->iter[k] += 1;
                 if (!isfinite(rr_new) || !isfinite(alpha)) bad = 1;
                 if (st->iter[k] >= st->maxit) capped = 1;
-                if (rr_new <= st->tol2bb)
+                if (rr_new <= st->tol2bb[k])
                     st->want_rel[k] = 1;  // parked until the host checks it
                 else
                     st->act[keep++] = k;
@@ -328,10 +327,11 @@ __global__ void k_b_CD(long n, size_t stride, float2* __restrict__ R, const floa
 // x_k += xl_k (FP64), xl_k = 0, for the listed slots
 struct SlotList {
     int k[STAG_MAXSHIFT];
+    double2* x[STAG_MAXSHIFT];
 };
-__global__ void k_b_accumulate(long n, size_t stride, double2* X, float2* XL, SlotList L) {
+__global__ void k_b_accumulate(long n, size_t stride, float2* XL, SlotList L) {
     const int k = L.k[blockIdx.y];
-    double2* x = X + k * stride;
+    double2* x = L.x[blockIdx.y];
     float2* xl = XL + k * stride;
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const float2 v = xl[i];
@@ -374,20 +374,20 @@ double env_d(const char* name, double dflt) {
 
 }  // namespace
 
-// FP64-accurate residuals r_k = b - (M + s_k) x_k for the listed shifts with
-// the float-float operator: FP32 copies into R + k*n3, |r_k|^2 into
-// dscal[100 + k] (read back, synchronising).
-int batched_true_residuals(stag_ctx* ctx, double mass, const double* shifts, const int* ks, int nk, const double2* b,
-                           const double2* X, float2* R, double* rr_out, cudaStream_t s) {
+// FP64-accurate residuals r_k = b_k - (M_ee + c_k - m^2) x_k for the listed
+// slots with the float-float operator: FP32 copies into R + k*n3, |r_k|^2
+// into dscal[100 + k] (read back, synchronising).
+int batched_true_residuals(stag_ctx* ctx, const RefSlots& S, const int* ks, int nk, float2* R, double* rr_out,
+                           cudaStream_t s) {
     const long n3 = 3L * ctx->g.Vh;
     double2* w64 = (double2*)ws_get(ctx, WS_W64, sizeof(double2) * n3);
     double2* t64 = (double2*)ws_get(ctx, WS_T64, sizeof(double2) * n3);
     if (!w64 || !t64) return stag_fail(ctx, STAG_ERR_OOM, "residual workspace");
     for (int i = 0; i < nk; i++) {
         const int k = ks[i];
-        int st = mee_apply(ctx, STAG_PREC_F64FF, mass * mass + shifts[k], X + k * n3, w64, t64, s);
+        int st = mee_apply(ctx, STAG_PREC_F64FF, S.c[k], S.x[k], w64, t64, s);
         if (st) return st;
-        k_b_residual<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, b, w64, R + k * n3, ctx->partials, ctx->counter,
+        k_b_residual<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, S.b[k], w64, R + k * n3, ctx->partials, ctx->counter,
                                                            ctx->dscal + 100 + k);
         STAG_LAUNCH_CHECK(ctx, "batched residual");
     }
@@ -408,7 +408,7 @@ struct BIter {
     Links U;
     float2 *R, *P, *W, *T, *XL;
     double* part;
-    int ny_hop, ny_blas, chunk, fused;
+    int ny_hop, ny_blas, chunk, fused, tpb;
 };
 
 void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
@@ -416,27 +416,27 @@ void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
     const Geom& g = ctx->g;
     const long n3 = 3L * g.Vh;
     const size_t stride = (size_t)n3;
-    const dim3 gh(nblocks(g.Vh, HOP_TPB), a.ny_hop), gb(ctx->num_sms, a.ny_blas);
+    const dim3 gh(nblocks(g.Vh, a.tpb), a.ny_hop), gb(ctx->num_sms, a.ny_blas);
     for (int i = 0; i < a.chunk; i++) {
         if (a.fused) {
             if (a.lp == LP32) {
-                k_b_A<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-                k_b_B3<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
+                k_b_A<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+                k_b_B3<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart,
                                                      ctx->counter);
             } else {
-                k_b_A<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-                k_b_B3<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
+                k_b_A<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+                k_b_B3<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart,
                                                      ctx->counter);
             }
             k_b_CD<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, ctx->counter);
             continue;
         }
         if (a.lp == LP32) {
-            k_b_A<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-            k_b_B<LP32><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
+            k_b_A<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+            k_b_B<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
         } else {
-            k_b_A<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-            k_b_B<LP16><<<gh, HOP_TPB, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
+            k_b_A<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+            k_b_B<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
         }
         k_b_C<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, a.part, ctx->counter);
         k_b_D<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.P, ctx->bcg, ctx->counter);
@@ -444,13 +444,12 @@ void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
 }
 }  // namespace
 
-// Refines the FP64 solutions X + k*n3 for the shifts ks[0..nk) (those whose
-// true residual rr[k] > tol^2 |b|^2 on entry; R + k*n3 must already hold
-// their FP32 residuals).  On return rr[k] holds each shift's final
-// FP64-accurate true residual^2.
-int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, const int* ks, int nk, const double2* b,
-                   double bb, double2* X, float2* R, double tol, int maxit, double* rr, int* iters, int* reliable,
-                   int* matvecs, cudaStream_t s) {
+// Refines the FP64 solutions S.x[k] of the slots ks[0..nk) (those whose true
+// residual rr[k] > tol^2 bb_k on entry; R + k*n3 must already hold their FP32
+// residuals).  On return rr[k] holds each slot's final FP64-accurate true
+// residual^2.
+int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int nk, float2* R, double tol, int maxit,
+                   double* rr, int* iters, int* reliable, int* matvecs, cudaStream_t s) {
     const Geom& g = ctx->g;
     const long n3 = 3L * g.Vh;
     const size_t vb = sizeof(float2) * n3 * STAG_MAXSHIFT;
@@ -463,7 +462,8 @@ int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, con
     it.XL = (float2*)ws_get(ctx, WS_XK32, vb);
     it.W = (float2*)ws_get(ctx, WS_BW, vb);
     it.T = (float2*)ws_get(ctx, WS_BT, vb);
-    const int nbx = nblocks(g.Vh, HOP_TPB);
+    it.tpb = hop_tpb(ctx, lp);
+    const int nbx = nblocks(g.Vh, 64);  // partials sized for the smallest block size
     it.part = (double*)ws_get(ctx, WS_BPART,
                               sizeof(double) * 4 * STAG_MAXSHIFT * (size_t)(nbx > ctx->num_sms ? nbx : ctx->num_sms));
     if (!it.P || !it.XL || !it.W || !it.T || !it.part) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
@@ -472,7 +472,6 @@ int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, con
     it.chunk = env_i("STAG_CHUNK", 16);
     it.fused = env_i("STAG_FUSED", 1);
     const double delta = env_d("STAG_RELIABLE_DELTA", 0.1);
-    const double tol2bb = tol * tol * bb;
     const int trace = env_i("STAG_TRACE_REFINE", 0);
 
     BCGState* hs = ctx->bcg_host;
@@ -481,20 +480,20 @@ int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, con
         const int k = ks[i];
         hs->act[i] = k;
         hs->rr[k] = hs->rr_max[k] = rr[k];
-        hs->c0[k] = mass * mass + shifts[k];
+        hs->c0[k] = S.c[k];
+        hs->tol2bb[k] = tol * tol * S.bb[k];
         STAG_CUDA(ctx, cudaMemsetAsync(it.XL + k * n3, 0, sizeof(float2) * n3, s));
         k_b_copy<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, R + k * n3, it.P + k * n3);
         STAG_LAUNCH_CHECK(ctx, "refine init");
     }
     hs->n_act = nk;
-    hs->tol2bb = tol2bb;
     hs->delta2 = delta * delta;
     hs->maxit = maxit;
     hs->live = nk > 0;
     STAG_CUDA(ctx, cudaMemcpyAsync(ctx->bcg, hs, sizeof(BCGState), cudaMemcpyHostToDevice, s));
 
     char key[64];
-    snprintf(key, sizeof key, "bcg_%d_%d_%d_%d", lp, nk, it.chunk, it.fused);
+    snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d", lp, nk, it.chunk, it.fused, it.tpb);
     int remaining = nk;
     int done[STAG_MAXSHIFT] = {0};
     while (remaining > 0) {
@@ -505,7 +504,7 @@ int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, con
         if (trace) {
             fprintf(stderr, "[refine] n_act %d live %d nonfinite %d |", hs->n_act, hs->live, hs->nonfinite);
             for (int i = 0; i < nk; i++)
-                fprintf(stderr, " k%d it%d rr%.2e a%.2e b%.2e p%d", ks[i], hs->iter[ks[i]], hs->rr[ks[i]] / bb,
+                fprintf(stderr, " k%d it%d rr%.2e a%.2e b%.2e p%d", ks[i], hs->iter[ks[i]], hs->rr[ks[i]] / S.bb[ks[i]],
                         hs->alpha[ks[i]], hs->beta[ks[i]], hs->want_rel[ks[i]]);
             fprintf(stderr, "\n");
         }
@@ -529,18 +528,21 @@ int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, con
         }
         if (nu > 0) {
             SlotList L;
-            for (int i = 0; i < nu; i++) L.k[i] = upd[i];
-            k_b_accumulate<<<dim3(ctx->num_sms, nu), BLAS_TPB, 0, s>>>(n3, (size_t)n3, X, it.XL, L);
+            for (int i = 0; i < nu; i++) {
+                L.k[i] = upd[i];
+                L.x[i] = S.x[upd[i]];
+            }
+            k_b_accumulate<<<dim3(ctx->num_sms, nu), BLAS_TPB, 0, s>>>(n3, (size_t)n3, it.XL, L);
             STAG_LAUNCH_CHECK(ctx, "refine accumulate");
             double rrt[STAG_MAXSHIFT];
-            if ((st = batched_true_residuals(ctx, mass, shifts, upd, nu, b, X, R, rrt, s))) return st;
+            if ((st = batched_true_residuals(ctx, S, upd, nu, R, rrt, s))) return st;
             *matvecs += nu;
             *reliable += nu;
             for (int i = 0; i < nu; i++) {
                 const int k = upd[i];
                 hs->want_rel[k] = 0;
                 rr[k] = rrt[k];
-                if (rrt[k] <= tol2bb || hs->iter[k] >= maxit) {
+                if (rrt[k] <= hs->tol2bb[k] || hs->iter[k] >= maxit) {
                     done[k] = 1;
                     remaining--;
                     in_act[k] = 0;

@@ -42,11 +42,40 @@ int rational_apply_int(stag_ctx* ctx, double mass, const stag_rational* r, const
     return blas_rational_combine(ctx, r->a0, r->a, r->n, src, X, out, s);
 }
 
-// F = total force dP/dtau = gauge force + sum_pf fermion force
-int total_force(stag_ctx* ctx, const stag_params* p, const TrajWork& w, long long* iters, cudaStream_t s) {
-    const int mixed = p->solve_mode_md == STAG_SOLVE_MIXED || p->solve_mode_md == STAG_SOLVE_MIXED_BF16;
-    int st = gauge_force_internal_prec(ctx, p->beta, w.F, 0, mixed, s);
-    if (st) return st;
+enum { FORCE_GAUGE = 1, FORCE_FERMION = 2, FORCE_ALL = 3 };
+
+// F = dP/dtau of the selected parts: gauge force and/or sum_pf fermion force
+int total_force(stag_ctx* ctx, const stag_params* p, const TrajWork& w, long long* iters, cudaStream_t s,
+                int parts = FORCE_ALL) {
+    const int mixed = p->solve_mode_md == STAG_SOLVE_MIXED || p->solve_mode_md == STAG_SOLVE_MIXED_BF16 ||
+                      p->solve_mode_md == STAG_SOLVE_LEARNED;
+    int st;
+    if (parts & FORCE_GAUGE) {
+        if ((st = gauge_force_internal_prec(ctx, p->beta, w.F, 0, mixed, s))) return st;
+    } else {
+        STAG_CUDA(ctx, cudaMemsetAsync(w.F, 0, sizeof(double) * 64 * (size_t)ctx->g.Vh, s));
+    }
+    if (!(parts & FORCE_FERMION)) return STAG_OK;
+    if (p->npf > 1 && p->solve_mode_md != STAG_SOLVE_LEARNED) {
+        // all pseudofermions in one batched solve (multi-RHS hops)
+        const long n3 = w.n3;
+        double2* XM = (double2*)ws_get(ctx, WS_MX, sizeof(double2) * n3 * STAG_MAXSHIFT * STAG_MAXRHS);
+        if (!XM) return stag_fail(ctx, STAG_ERR_OOM, "force workspace");
+        const double2* srcs[STAG_MAXRHS];
+        for (int pf = 0; pf < p->npf; pf++) srcs[pf] = w.phi + pf * n3;
+        stag_solve_info infos[STAG_MAXRHS];
+        st = multishift_solve_multi(ctx, p->mass, p->npf, p->force.n, p->force.b, srcs, XM, p->tol_md, p->maxit,
+                                    p->solve_mode_md, infos, s);
+        for (int pf = 0; pf < p->npf; pf++) {
+            *iters += infos[pf].iters;
+            for (int k = 0; k < p->force.n; k++) *iters += infos[pf].refine_iters[k];
+        }
+        if (st) return st;
+        for (int pf = 0; pf < p->npf; pf++)
+            if ((st = fermion_force_assemble(ctx, &p->force, XM + (size_t)pf * STAG_MAXSHIFT * n3, w.F, 1, s)))
+                return st;
+        return STAG_OK;
+    }
     for (int pf = 0; pf < p->npf; pf++) {
         stag_solve_info info;
         double2* sols[STAG_MAXSHIFT];
@@ -84,34 +113,66 @@ int hamiltonian(stag_ctx* ctx, const stag_params* p, const TrajWork& w, double* 
 }
 
 // Integrate over tau: leapfrog P(e/2) Q(e) P(e/2) or Omelyan 2MN
-// P(l e) Q(e/2) P((1-2l) e) Q(e/2) P(l e), merged end half-steps.
+// P(l e) Q(e/2) P((1-2l) e) Q(e/2) P(l e), merged end half-steps.  With
+// ngauge > 0 (multi-step scheme) P(.) uses the fermion force only and each
+// Q(h) is ngauge inner steps of the same scheme over h with the gauge force
+// (inner end half-steps merged within one Q(h)).
 int md_integrate(stag_ctx* ctx, const stag_params* p, const TrajWork& w, long long* iters, int* nforce,
                  cudaStream_t s) {
     const double eps = p->tau / p->nsteps;
+    const double lam = p->lambda;
+    const int multi = p->ngauge > 0;
     int st;
-#define FORCE_STEP(coef)                                                   \
-    do {                                                                   \
-        if ((st = total_force(ctx, p, w, iters, s))) return st;            \
-        (*nforce)++;                                                       \
-        if ((st = update_momenta(ctx, w.F, (coef), s))) return st;         \
+#define FORCE_STEP(coef)                                                                          \
+    do {                                                                                          \
+        if ((st = total_force(ctx, p, w, iters, s, multi ? FORCE_FERMION : FORCE_ALL))) return st; \
+        (*nforce)++;                                                                              \
+        if ((st = update_momenta(ctx, w.F, (coef), s))) return st;                                \
     } while (0)
+#define GAUGE_STEP(coef)                                                             \
+    do {                                                                             \
+        if ((st = total_force(ctx, p, w, iters, s, FORCE_GAUGE))) return st;         \
+        if ((st = update_momenta(ctx, w.F, (coef), s))) return st;                   \
+    } while (0)
+    // position update over h: one link update, or the inner gauge scheme
+    auto move = [&](double h) -> int {
+        if (!multi) return update_links(ctx, h, s);
+        const int ng = p->ngauge;
+        const double d = h / ng;
+        if (p->integrator == STAG_INT_LEAPFROG) {
+            GAUGE_STEP(0.5 * d);
+            for (int j = 0; j < ng; j++) {
+                if ((st = update_links(ctx, d, s))) return st;
+                GAUGE_STEP(j == ng - 1 ? 0.5 * d : d);
+            }
+        } else {
+            GAUGE_STEP(lam * d);
+            for (int j = 0; j < ng; j++) {
+                if ((st = update_links(ctx, 0.5 * d, s))) return st;
+                GAUGE_STEP((1.0 - 2.0 * lam) * d);
+                if ((st = update_links(ctx, 0.5 * d, s))) return st;
+                GAUGE_STEP(j == ng - 1 ? lam * d : 2.0 * lam * d);
+            }
+        }
+        return STAG_OK;
+    };
     if (p->integrator == STAG_INT_LEAPFROG) {
         FORCE_STEP(0.5 * eps);
         for (int k = 0; k < p->nsteps; k++) {
-            if ((st = update_links(ctx, eps, s))) return st;
+            if ((st = move(eps))) return st;
             FORCE_STEP(k == p->nsteps - 1 ? 0.5 * eps : eps);
         }
     } else {
-        const double lam = p->lambda;
         FORCE_STEP(lam * eps);
         for (int k = 0; k < p->nsteps; k++) {
-            if ((st = update_links(ctx, 0.5 * eps, s))) return st;
+            if ((st = move(0.5 * eps))) return st;
             FORCE_STEP((1.0 - 2.0 * lam) * eps);
-            if ((st = update_links(ctx, 0.5 * eps, s))) return st;
+            if ((st = move(0.5 * eps))) return st;
             FORCE_STEP(k == p->nsteps - 1 ? lam * eps : 2.0 * lam * eps);
         }
     }
 #undef FORCE_STEP
+#undef GAUGE_STEP
     return STAG_OK;
 }
 
@@ -169,7 +230,7 @@ int rhmc_trajectory(stag_ctx* ctx, const stag_params* p, stag_traj_info* out, cu
     const double dH = H1 - H0;
     const double u = ctx->hscal[60];
     if (!isfinite(dH)) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite dH");
-    const int acc = (u < exp(-dH)) ? 1 : 0;
+    const int acc = (p->no_metropolis || u < exp(-dH)) ? 1 : 0;
     if (!acc) {
         STAG_CUDA(ctx, cudaMemcpyAsync(ctx->U64, ctx->U64_save, sizeof(double2) * 48 * (size_t)ctx->g.Vh,
                                        cudaMemcpyDeviceToDevice, s));

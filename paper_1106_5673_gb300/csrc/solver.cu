@@ -14,6 +14,7 @@
 // is captured once per context as a CUDA graph.  Kernels started after the
 // stop flag return immediately.
 #include "hop.cuh"
+#include "ms_common.cuh"
 #include "stag_internal.h"
 
 #include <chrono>
@@ -51,7 +52,7 @@ static Links make_links(const stag_ctx* ctx, int lp) {
 // ============================================================== multi-shift kernels
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_ms_A(Geom g, Links U,
+__global__ void __launch_bounds__(256) k_ms_A(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ t, const int* live) {
     if (!*live) return;
@@ -87,7 +88,7 @@ STAG_D double mee_second_hop(const Geom& g, Links U, const typename VT<R>::T* t,
 }
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_ms_B(Geom g, Links U,
+__global__ void __launch_bounds__(256) k_ms_B(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ t,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ w, MSState* st, double* partials,
@@ -134,11 +135,11 @@ __global__ void __launch_bounds__(HOP_TPB) k_ms_B(Geom g, Links U,
 // (no separate pass over r), then every scalar of the iteration: the shifted
 // zeta, a_k, b_k, per-shift convergence and the stop flag.
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_ms_B3(Geom g, Links U, const typename VT<R>::T* __restrict__ t,
+__global__ void __launch_bounds__(256) k_ms_B3(Geom g, Links U, const typename VT<R>::T* __restrict__ t,
                                                    const typename VT<R>::T* __restrict__ p,
                                                    const typename VT<R>::T* __restrict__ r,
                                                    typename VT<R>::T* __restrict__ w, MSState* st, double* partials,
-                                                   unsigned int* counter) {
+                                                   double* gpart, unsigned int* counter) {
     if (!st->live) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     double pw = 0.0, rw = 0.0, ww = 0.0, rr = 0.0;
@@ -169,62 +170,8 @@ __global__ void __launch_bounds__(HOP_TPB) k_ms_B3(Geom g, Links U, const typena
 #pragma unroll
         for (int j = 0; j < 4; j++) partials[j * gridDim.x + blockIdx.x] = v[j];
     }
-    if (last_block(counter)) {
-        __shared__ double s_t[4];
-        reduce_series(partials, 4, gridDim.x, s_t);
-        const double t0 = s_t[0], t1 = s_t[1], t2 = s_t[2], t3 = s_t[3];
-        __shared__ double s_alpha, s_beta, s_rr;
-        __shared__ int s_iter;
-        if (threadIdx.x == 0) {
-            // |r_j|^2 freshly reduced (t3), so the expansion of |r_{j+1}|^2
-            // carries one step of rounding, not an accumulated recursion
-            const double alpha = t3 / t0;
-            double rr_new = t3 - 2.0 * alpha * t1 + alpha * alpha * t2;
-            if (rr_new < 0.0) rr_new = 0.0;
-            s_alpha = alpha;
-            s_rr = rr_new;
-            s_beta = rr_new / t3;
-            s_iter = st->iter + 1;
-            st->pw = t0;
-            st->alpha = alpha;
-        }
-        __syncthreads();
-        const int k = threadIdx.x;
-        int act = 0;
-        if (k < st->n) {
-            if (st->active[k]) {
-                const double alpha = s_alpha;
-                const double d = st->shifts[k] - st->shifts[st->base];
-                const double zo = st->zeta_old[k], z = st->zeta[k], ao = st->alpha_old;
-                const double den = zo * ao * (1.0 + d * alpha) + alpha * st->beta_old * (zo - z);
-                const double zn = z * zo * ao / den;
-                const double ratio = zn / z;
-                st->ak[k] = alpha * ratio;
-                st->bk[k] = s_beta * ratio * ratio;
-                st->zeta_old[k] = z;
-                st->zeta[k] = zn;
-                st->upd_x[k] = 1;
-                st->iters_shift[k] = s_iter;
-                st->active[k] = (zn * zn * s_rr > st->tol2bb) ? 1 : 0;
-            } else {
-                st->upd_x[k] = 0;
-                st->ak[k] = 0.0;
-            }
-            act = st->active[k];
-        }
-        const int n_active = __syncthreads_count(act);
-        if (threadIdx.x == 0) {
-            st->iter = s_iter;
-            st->n_active = n_active;
-            st->beta = s_beta;
-            st->rr = s_rr;
-            st->alpha_old = s_alpha;
-            st->beta_old = s_beta;
-            const int bad = !isfinite(s_rr) || !isfinite(s_beta) || !isfinite(s_alpha);
-            if (bad) st->nonfinite = 1;
-            st->stop_next = (n_active == 0 || s_iter >= st->maxit || bad) ? 1 : 0;
-        }
-    }
+    __shared__ double s_t[4];
+    if (grid_reduce_series(partials, gpart, counter, 4, s_t)) ms_scalar_update(st, s_t[0], s_t[1], s_t[2], s_t[3]);
 }
 
 // CD: r -= alpha w; p = r + beta p; x_k += a_k p_k; p_k = zeta_k r + b_k p_k
@@ -232,42 +179,8 @@ template <typename V2, typename R>
 __global__ void k_ms_CD(long n, long stride, V2* __restrict__ r, const V2* __restrict__ w, V2* __restrict__ p,
                         V2* __restrict__ pk, V2* __restrict__ xk, MSState* st, unsigned int* counter) {
     if (!st->live) return;
-    __shared__ R s_ak[STAG_MAXSHIFT], s_bk[STAG_MAXSHIFT], s_z[STAG_MAXSHIFT];
-    __shared__ int s_ux[STAG_MAXSHIFT], s_act[STAG_MAXSHIFT];
-    const int ns = st->n;
-    if (threadIdx.x < ns) {
-        s_ak[threadIdx.x] = (R)st->ak[threadIdx.x];
-        s_bk[threadIdx.x] = (R)st->bk[threadIdx.x];
-        s_z[threadIdx.x] = (R)st->zeta[threadIdx.x];
-        s_ux[threadIdx.x] = st->upd_x[threadIdx.x];
-        s_act[threadIdx.x] = st->active[threadIdx.x];
-    }
-    __syncthreads();
-    const R alpha = (R)st->alpha, beta = (R)st->beta;
-    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-        V2 rv = r[i];
-        const V2 wv = w[i];
-        rv.x -= alpha * wv.x;
-        rv.y -= alpha * wv.y;
-        r[i] = rv;
-        V2 pv = p[i];
-        pv.x = rv.x + beta * pv.x;
-        pv.y = rv.y + beta * pv.y;
-        p[i] = pv;
-        for (int k = 0; k < ns; k++) {
-            if (!s_ux[k]) continue;
-            V2 q = pk[k * stride + i];
-            V2 x = xk[k * stride + i];
-            x.x += s_ak[k] * q.x;
-            x.y += s_ak[k] * q.y;
-            xk[k * stride + i] = x;
-            if (s_act[k]) {
-                q.x = s_z[k] * rv.x + s_bk[k] * q.x;
-                q.y = s_z[k] * rv.y + s_bk[k] * q.y;
-                pk[k * stride + i] = q;
-            }
-        }
-    }
+    ms_vector_update<V2, R>(n, stride, blockIdx.x * (long)blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x, r,
+                            w, p, pk, xk, st);
     if (last_block(counter)) {
         if (threadIdx.x == 0 && st->stop_next) st->live = 0;
     }
@@ -478,7 +391,7 @@ __global__ void k_cg_D(long n, const V2* __restrict__ r, V2* __restrict__ p, CGS
 }
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_cg_A(Geom g, Links U,
+__global__ void __launch_bounds__(256) k_cg_A(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ t, const CGState* st) {
     if (!st->live) return;
@@ -492,7 +405,7 @@ __global__ void __launch_bounds__(HOP_TPB) k_cg_A(Geom g, Links U,
 }
 
 template <typename R, int LP>
-__global__ void __launch_bounds__(HOP_TPB) k_cg_B(Geom g, Links U,
+__global__ void __launch_bounds__(256) k_cg_B(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ t,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ w, CGState* st, double* partials,
@@ -578,17 +491,18 @@ void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
     typedef typename VT<R>::T V2;
     const Geom& g = ctx->g;
     const long n = 3L * g.Vh;
-    const int nb_hop = nblocks(g.Vh, HOP_TPB);
+    const int tpb = hop_tpb(ctx, LP);
+    const int nb_hop = nblocks(g.Vh, tpb);
     const int nb_blas = ctx->num_sms * 4;
-    k_ms_A<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, &ctx->ms->live);
+    k_ms_A<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, &ctx->ms->live);
     if (fused_iter()) {
-        k_ms_B3<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
-                                                 ctx->ms, ctx->partials, ctx->counter);
+        k_ms_B3<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
+                                                 ctx->ms, ctx->partials, ctx->gpart, ctx->counter);
         k_ms_CD<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, (V2*)b.pk,
                                                    (V2*)b.xk, ctx->ms, ctx->counter);
         return;
     }
-    k_ms_B<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (V2*)b.w, ctx->ms,
+    k_ms_B<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (V2*)b.w, ctx->ms,
                                             ctx->partials, ctx->counter);
     k_ms_C<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (V2*)b.r, (const V2*)b.w, ctx->ms, ctx->partials, ctx->counter);
     k_ms_D<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, n, (const V2*)b.r, (V2*)b.p, (V2*)b.pk, (V2*)b.xk, ctx->ms,
@@ -600,10 +514,11 @@ void launch_cg_iter(stag_ctx* ctx, Links U, void* r, void* p, void* w, void* t, 
     typedef typename VT<R>::T V2;
     const Geom& g = ctx->g;
     const long n = 3L * g.Vh;
-    const int nb_hop = nblocks(g.Vh, HOP_TPB);
+    const int tpb = hop_tpb(ctx, LP);
+    const int nb_hop = nblocks(g.Vh, tpb);
     const int nb_blas = ctx->num_sms * 4;
-    k_cg_A<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)p, (V2*)t, ctx->cg);
-    k_cg_B<R, LP><<<nb_hop, HOP_TPB, 0, s>>>(g, U, (const V2*)t, (const V2*)p, (V2*)w, ctx->cg, ctx->partials,
+    k_cg_A<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)p, (V2*)t, ctx->cg);
+    k_cg_B<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)t, (const V2*)p, (V2*)w, ctx->cg, ctx->partials,
                                             ctx->counter);
     k_cg_C<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (V2*)r, (const V2*)w, (const V2*)p, (V2*)x, ctx->cg,
                                               ctx->partials, ctx->counter);
@@ -707,7 +622,8 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
 
     const int chunk = env_int("STAG_CHUNK", 16);
     char key[64];
-    snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), bf.xk);
+    snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), hop_tpb(ctx, LP),
+             bf.xk);
     int guard = 0;
     for (;;) {
         st = run_chunk(ctx, key, (fused_iter() ? 3 : 4) * chunk, [&](cudaStream_t cs) {
@@ -779,7 +695,7 @@ int refine_shift(stag_ctx* ctx, double mass, double shift, const double2* b, dou
     hs->live = 1;
     STAG_CUDA(ctx, cudaMemcpyAsync(ctx->cg, hs, sizeof(CGState), cudaMemcpyHostToDevice, s));
     char key[64];
-    snprintf(key, sizeof key, "cg_%d_%d", LP, chunk);
+    snprintf(key, sizeof key, "cg_%d_%d_%d", LP, chunk, hop_tpb(ctx, LP));
     int total_iter = 0;
     for (;;) {
         st = run_chunk(ctx, key, 4 * chunk, [&](cudaStream_t cs) {
@@ -827,6 +743,119 @@ int run_graph_chunk(stag_ctx* ctx, const char* key, int nkernels, void (*enqueue
     return run_chunk(ctx, std::string(key), nkernels, [&](cudaStream_t cs) { enqueue(ctx, arg, cs); }, s);
 }
 
+// FP64-accurate residuals (float-float operator) of the FP32 multi-shift
+// solutions X[k], then the batched refinement of the shifts above tol; fills
+// info's residuals and refinement counts, returns STAG_OK or STAG_ERR_NOCONV.
+static int finish_batched(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src, double2* X,
+                          double tol, int maxit, stag_solve_info* info, cudaStream_t s) {
+    const long n3 = 3L * ctx->g.Vh;
+    float2* R = (float2*)ws_get(ctx, WS_BR, sizeof(float2) * n3 * STAG_MAXSHIFT);
+    if (!R) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
+    int st;
+    if ((st = blas_dot_re(ctx, STAG_PREC_F64, src, src, ctx->dscal + 1, s))) return st;
+    RefSlots S;
+    int all[STAG_MAXSHIFT];
+    for (int k = 0; k < n; k++) {
+        all[k] = k;
+        S.b[k] = src;
+        S.x[k] = X + k * n3;
+        S.c[k] = mass * mass + shifts[k];
+    }
+    double rr[STAG_MAXSHIFT];
+    if ((st = batched_true_residuals(ctx, S, all, n, R, rr, s))) return st;
+    info->matvecs += n;
+    const double bb = ctx->hscal[1];
+    for (int k = 0; k < n; k++) S.bb[k] = bb;
+    int ks[STAG_MAXSHIFT], nk = 0;
+    for (int k = 0; k < n; k++)
+        if (bb > 0.0 && rr[k] > tol * tol * bb) ks[nk++] = k;
+    if (nk > 0) {
+        int its[STAG_MAXSHIFT] = {0}, rel = 0, mv = 0;
+        // the refinement always uses FP32 links: BF16's ~4e-3 operator error times
+        // the condition number of the light shifts exceeds one, and an inner
+        // iteration that far from the true operator does not converge
+        st = refine_batched(ctx, LP32, S, ks, nk, R, tol, maxit, rr, its, &rel, &mv, s);
+        if (st) return st;
+        for (int i = 0; i < nk; i++) info->refine_iters[ks[i]] = its[ks[i]];
+        info->reliable_updates += rel;
+        info->matvecs += mv;
+    }
+    int status = STAG_OK;
+    for (int k = 0; k < n; k++) {
+        info->true_resid[k] = (bb > 0.0) ? sqrt(rr[k] / bb) : 0.0;
+        if (!isfinite(info->true_resid[k])) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite solution");
+        if (rr[k] > tol * tol * bb * 1.0000001) status = STAG_ERR_NOCONV;
+    }
+    return status;
+}
+
+// STAG_SOLVE_LEARNED: the lightest shift by the network-preconditioned flexible
+// CG, the others by the FP32 multi-shift (based at the second lightest shift)
+// and batched refinement.  Falls back to the MIXED solver over all shifts when
+// the flexible CG misses tol within its cap.  X[k] receives shift k.
+static int learned_solve(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src, double2* X,
+                         double tol, int maxit, stag_solve_info* info, cudaStream_t s) {
+    if (!ctx->net) return stag_fail(ctx, STAG_ERR_STATE, "STAG_SOLVE_LEARNED needs a network (stag_ctx_set_net)");
+    const long n3 = 3L * ctx->g.Vh;
+    const size_t vb64 = sizeof(double2) * n3;
+    int kmin = 0;
+    for (int k = 1; k < n; k++)
+        if (shifts[k] < shifts[kmin]) kmin = k;
+    double2* XL = (double2*)ws_get(ctx, WS_LX, vb64);
+    if (!XL) return stag_fail(ctx, STAG_ERR_OOM, "learned-mode workspace");
+    int fit = 0;
+    double ftr = 0.0;
+    const int cap = env_int("STAG_FCG_MAXIT", 2000);
+    int st = fcg_solve(ctx, ctx->net, mass, shifts[kmin], src, XL, tol, cap < maxit ? cap : maxit, &fit, &ftr, s);
+    info->matvecs += fit + 1;
+    if (st == STAG_ERR_NOCONV) {  // fallback: the plain mixed solver over all shifts
+        stag_solve_info fb;
+        memset(&fb, 0, sizeof(fb));
+        if ((st = ms_core<float, LP32>(ctx, mass, n, shifts, src, X, fmax(tol, env_dbl("STAG_MS_TOL32", 1e-6)), maxit,
+                                       &fb, s)))
+            return st;
+        st = finish_batched(ctx, mass, n, shifts, src, X, tol, maxit, &fb, s);
+        fb.matvecs += info->matvecs;
+        fb.refine_iters[kmin] += fit;
+        *info = fb;
+        return st;
+    }
+    if (st) return st;
+    // the other shifts, compacted into X[0 .. n-2], then rotated into place
+    double sh2[STAG_MAXSHIFT];
+    int m = 0;
+    for (int k = 0; k < n; k++)
+        if (k != kmin) sh2[m++] = shifts[k];
+    stag_solve_info i2;
+    memset(&i2, 0, sizeof(i2));
+    if (m > 0) {
+        if ((st = ms_core<float, LP32>(ctx, mass, m, sh2, src, X, fmax(tol, env_dbl("STAG_MS_TOL32", 1e-6)), maxit,
+                                       &i2, s)))
+            return st;
+        const int st2 = finish_batched(ctx, mass, m, sh2, src, X, tol, maxit, &i2, s);
+        if (st2 && st2 != STAG_ERR_NOCONV) return st2;
+        st = st2;
+    }
+    for (int k = n - 1; k > kmin; k--)
+        STAG_CUDA(ctx, cudaMemcpyAsync(X + k * n3, X + (k - 1) * n3, vb64, cudaMemcpyDeviceToDevice, s));
+    STAG_CUDA(ctx, cudaMemcpyAsync(X + kmin * n3, XL, vb64, cudaMemcpyDeviceToDevice, s));
+    info->iters = i2.iters;
+    info->reliable_updates = i2.reliable_updates;
+    info->matvecs += i2.matvecs;
+    for (int k = 0, j = 0; k < n; k++) {
+        if (k == kmin) {
+            info->iters_shift[k] = fit;
+            info->true_resid[k] = ftr;
+            continue;
+        }
+        info->iters_shift[k] = i2.iters_shift[j];
+        info->refine_iters[k] = i2.refine_iters[j];
+        info->true_resid[k] = i2.true_resid[j];
+        j++;
+    }
+    return st;
+}
+
 int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src,
                      double2* const* sols, double tol, int maxit, int mode, stag_solve_info* info, cudaStream_t s) {
     if (n < 1 || n > STAG_MAXSHIFT) return stag_fail(ctx, STAG_ERR_ARG, "number of shifts %d out of range", n);
@@ -844,11 +873,16 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
     double2* X = (double2*)ws_get(ctx, WS_FX, vb64 * STAG_MAXSHIFT);
     if (!X) return stag_fail(ctx, STAG_ERR_OOM, "solution workspace");
     int st;
+    if (!ctx->tuned && env_int("STAG_AUTOTUNE", 1)) {  // first solve on this context
+        if ((st = autotune_hops(ctx, s))) return st;
+    }
     const int check_prec = (mode == STAG_SOLVE_F64) ? STAG_PREC_F64 : STAG_PREC_F64FF;
     if (mode == STAG_SOLVE_F64) {
         st = ms_core<double, LP64>(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
     } else if (mode == STAG_SOLVE_F64FF) {
         st = ms_core<double, LPFF>(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
+    } else if (mode == STAG_SOLVE_LEARNED) {
+        st = STAG_OK;  // learned_solve below runs its own solvers
     } else if (mode == STAG_SOLVE_MIXED || mode == STAG_SOLVE_MIXED_BF16) {
         const double tol_ms = fmax(tol, env_dbl("STAG_MS_TOL32", 1e-6));
         if (mode == STAG_SOLVE_MIXED)
@@ -861,38 +895,11 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
     if (st) return st;
 
     const int batched = (mode == STAG_SOLVE_MIXED || mode == STAG_SOLVE_MIXED_BF16) && env_int("STAG_BATCHED", 1);
-    if (batched) {
-        // FP64-accurate residuals of all shifts (float-float operator), then the
-        // batched refinement of those above tolerance
-        float2* R = (float2*)ws_get(ctx, WS_BR, sizeof(float2) * n3 * STAG_MAXSHIFT);
-        if (!R) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
-        if ((st = blas_dot_re(ctx, STAG_PREC_F64, src, src, ctx->dscal + 1, s))) return st;
-        int all[STAG_MAXSHIFT];
-        for (int k = 0; k < n; k++) all[k] = k;
-        double rr[STAG_MAXSHIFT];
-        if ((st = batched_true_residuals(ctx, mass, shifts, all, n, src, X, R, rr, s))) return st;
-        info->matvecs += n;
-        const double bb = ctx->hscal[1];
-        int ks[STAG_MAXSHIFT], nk = 0;
-        for (int k = 0; k < n; k++)
-            if (bb > 0.0 && rr[k] > tol * tol * bb) ks[nk++] = k;
-        if (nk > 0) {
-            int its[STAG_MAXSHIFT] = {0}, rel = 0, mv = 0;
-            // the refinement always uses FP32 links: BF16's ~4e-3 operator error times
-            // the condition number of the light shifts exceeds one, and an inner
-            // iteration that far from the true operator does not converge
-            st = refine_batched(ctx, LP32, mass, shifts, ks, nk, src, bb, X, R, tol, maxit, rr, its, &rel, &mv, s);
-            if (st) return st;
-            for (int i = 0; i < nk; i++) info->refine_iters[ks[i]] = its[ks[i]];
-            info->reliable_updates += rel;
-            info->matvecs += mv;
-        }
-        int status = STAG_OK;
-        for (int k = 0; k < n; k++) {
-            info->true_resid[k] = (bb > 0.0) ? sqrt(rr[k] / bb) : 0.0;
-            if (!isfinite(info->true_resid[k])) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite solution");
-            if (rr[k] > tol * tol * bb * 1.0000001) status = STAG_ERR_NOCONV;
-        }
+    if (batched || mode == STAG_SOLVE_LEARNED) {
+        int status = (mode == STAG_SOLVE_LEARNED)
+                         ? learned_solve(ctx, mass, n, shifts, src, X, tol, maxit, info, s)
+                         : finish_batched(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
+        if (status && status != STAG_ERR_NOCONV) return status;
         if (sols) {
             for (int k = 0; k < n; k++)
                 if (sols[k] && sols[k] != X + k * n3)

@@ -29,6 +29,11 @@ enum WsSlot {
     WS_PHI, WS_RGAUSS, WS_RAT,            // trajectory: pseudofermions, R, r(M) phi
     WS_FORCE,                             // force accumulator [4][2][8][Vh] doubles
     WS_BR, WS_BW, WS_BT, WS_BPART,        // batched refinement: residuals, M p, odd temp, partials
+    WS_TUNE,                              // autotuner test vectors
+    WS_MR, WS_MP, WS_MW, WS_MT,           // batched multi-system solver: per-system vectors
+    WS_MPK, WS_MXK, WS_MX,                // per-system shifted p_k / x_k (low precision), FP64 solutions
+    WS_FCG,                               // flexible CG vectors
+    WS_LX,                                // learned mode: solution of the lightest shift
     WS_NSLOTS
 };
 
@@ -56,7 +61,7 @@ struct CGState {
 struct BCGState {
     double rr[STAG_MAXSHIFT], rr_prev[STAG_MAXSHIFT], rr_max[STAG_MAXSHIFT];
     double alpha[STAG_MAXSHIFT], beta[STAG_MAXSHIFT], c0[STAG_MAXSHIFT];
-    double tol2bb, delta2;
+    double tol2bb[STAG_MAXSHIFT], delta2;
     int act[STAG_MAXSHIFT];       // active RHS slots, compacted; n_act of them
     int uact[STAG_MAXSHIFT];      // slots updated by the current iteration (fused path)
     int want_rel[STAG_MAXSHIFT];  // per slot: reliable update requested
@@ -76,7 +81,9 @@ struct stag_ctx {
     double* mom;        // [4][2][8][Vh]
     int gauge_loaded;
     double* partials;   // reduction partials
-    unsigned int* counter;
+    unsigned int* counter;  // last-block counters ([0] and the group counters of grid_reduce_series)
+    size_t counter_bytes;
+    double* gpart;      // group sums of grid_reduce_series
     double* dscal;      // device scalar area (STAG_NSCAL doubles)
     double* hscal;      // pinned host mirror of dscal
     MSState* ms;        // device multi-shift state
@@ -85,13 +92,24 @@ struct stag_ctx {
     CGState* cg_host;   // pinned host mirror
     BCGState* bcg;      // device batched-refinement state
     BCGState* bcg_host; // pinned host mirror
+    MSState* msm;       // device states of the batched multi-system solver [STAG_MAXRHS]
+    MSState* msm_host;  // pinned host mirror
+    double* mm_partials;  // its reduction partials
     void* ws[WS_NSLOTS];
     size_t ws_bytes[WS_NSLOTS];
     size_t fixed_bytes;
     std::map<std::string, cudaGraphExec_t> graphs;
     int num_sms;
     long long nlaunch;  // kernels launched (graph nodes counted individually)
+    int tpb[4];         // tuned threads per block of the hop kernels, per link precision (0: default)
+    int tuned;
+    stag_net* net;      // preconditioner of STAG_SOLVE_LEARNED (borrowed)
 };
+
+// threads per block of the hop kernels for link precision lp (autotuned, else 128)
+static inline int hop_tpb(const stag_ctx* c, int lp) { return c->tpb[lp] > 0 ? c->tpb[lp] : 128; }
+void ctx_clear_graphs(stag_ctx* ctx);
+int autotune_hops(stag_ctx* ctx, cudaStream_t s);
 
 // ---------------------------------------------------------------- utilities (capi.cu)
 int stag_fail(stag_ctx* ctx, int code, const char* fmt, ...);
@@ -148,11 +166,38 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
                      cudaStream_t s);
 
 // ---------------------------------------------------------------- refine.cu
-int batched_true_residuals(stag_ctx* ctx, double mass, const double* shifts, const int* ks, int nk, const double2* b,
-                           const double2* X, float2* R, double* rr_out, cudaStream_t s);
-int refine_batched(stag_ctx* ctx, int lp, double mass, const double* shifts, const int* ks, int nk, const double2* b,
-                   double bb, double2* X, float2* R, double tol, int maxit, double* rr, int* iters, int* reliable,
-                   int* matvecs, cudaStream_t s);
+// Systems of a batched refinement: slot k solves (M_ee + c_k - m^2) x_k = b_k,
+// i.e. M_ee with diagonal c_k = m^2 + shift; bb_k = |b_k|^2.
+struct RefSlots {
+    const double2* b[STAG_MAXSHIFT];
+    double2* x[STAG_MAXSHIFT];
+    double c[STAG_MAXSHIFT];
+    double bb[STAG_MAXSHIFT];
+};
+int batched_true_residuals(stag_ctx* ctx, const RefSlots& S, const int* ks, int nk, float2* R, double* rr_out,
+                           cudaStream_t s);
+int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int nk, float2* R, double tol, int maxit,
+                   double* rr, int* iters, int* reliable, int* matvecs, cudaStream_t s);
+
+// ---------------------------------------------------------------- msmulti.cu
+int multishift_solve_multi(stag_ctx* ctx, double mass, int nsys, int n, const double* shifts,
+                           const double2* const* srcs, double2* X, double tol, int maxit, int mode,
+                           stag_solve_info* infos, cudaStream_t s);
+
+// ---------------------------------------------------------------- gcnn.cu
+int net_create(stag_ctx* ctx, unsigned seed, stag_net** out);
+void net_destroy(stag_net* net);
+int net_apply(stag_net* net, const double2* b, double2* z, cudaStream_t s);
+int net_loss_grad(stag_net* net, int npairs, const double2* const* bs, const double2* const* xs, double* loss,
+                  cudaStream_t s);
+int net_train(stag_net* net, int npairs, const double2* const* bs, const double2* const* xs, int epochs, int batch,
+              double lr, double* loss_out, cudaStream_t s);
+int net_get_weights(stag_net* net, int layer, float* host);
+int net_set_weights(stag_net* net, int layer, const float* host);
+int net_get_grads(stag_net* net, int layer, float* host);
+int net_nweights(const stag_net* net, int layer);
+int fcg_solve(stag_ctx* ctx, stag_net* net, double mass, double shift, const double2* b, double2* x, double tol,
+              int maxit, int* iters, double* true_resid, cudaStream_t s);
 
 // ---------------------------------------------------------------- force.cu
 // F (internal) (+)= fermion force for sum_k a_k X_k, Y_k = D_oe X_k; X contiguous FP64

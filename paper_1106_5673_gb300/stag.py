@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libstag.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOCONV, ERR_NONFINITE, ERR_OOM, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
 PREC_F64, PREC_F32, PREC_BF16, PREC_F64FF = 0, 1, 2, 3
-SOLVE_F64, SOLVE_MIXED, SOLVE_MIXED_BF16, SOLVE_F64FF = 0, 1, 2, 3
+SOLVE_F64, SOLVE_MIXED, SOLVE_MIXED_BF16, SOLVE_F64FF, SOLVE_LEARNED = 0, 1, 2, 3, 4
 INT_LEAPFROG, INT_OMELYAN = 0, 1
 MAXSHIFT = 32
 MAXPF = 8
@@ -66,7 +66,8 @@ class Params(C.Structure):
                 ("npf", C.c_int), ("hb", Rational), ("act", Rational), ("force", Rational),
                 ("tol_md", C.c_double), ("tol_metro", C.c_double),
                 ("solve_mode_md", C.c_int), ("solve_mode_metro", C.c_int), ("maxit", C.c_int),
-                ("seed", C.c_uint32), ("traj", C.c_uint32), ("use_graphs", C.c_int)]
+                ("seed", C.c_uint32), ("traj", C.c_uint32), ("use_graphs", C.c_int),
+                ("ngauge", C.c_int), ("no_metropolis", C.c_int)]
 
 
 class TrajInfo(C.Structure):
@@ -90,6 +91,7 @@ _SIGS = {
     "stag_last_error": (C.c_char_p, [_vp]),
     "stag_ctx_device_bytes": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "stag_ctx_launch_count": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
+    "stag_autotune": (C.c_int, [_vp, C.POINTER(C.c_int), _vp]),
     "stag_load_gauge": (C.c_int, [_vp, _vp, C.c_int, _vp]),
     "stag_store_gauge": (C.c_int, [_vp, _vp, C.c_int, _vp]),
     "stag_load_momenta": (C.c_int, [_vp, _vp, C.c_int, _vp]),
@@ -101,6 +103,9 @@ _SIGS = {
     "stag_apply_M": (C.c_int, [_vp, C.c_double, _vp, _vp, C.c_int, _vp]),
     "stag_multishift_solve": (C.c_int, [_vp, C.c_double, C.c_int, _dp, _vp, C.POINTER(_vp),
                                         C.c_double, C.c_int, C.c_int, C.POINTER(SolveInfo), _vp]),
+    "stag_multishift_solve_multi": (C.c_int, [_vp, C.c_double, C.c_int, C.c_int, _dp,
+                                              C.POINTER(_vp), C.POINTER(_vp), C.c_double, C.c_int,
+                                              C.c_int, C.POINTER(SolveInfo), _vp]),
     "stag_rational_apply": (C.c_int, [_vp, C.c_double, C.POINTER(Rational), _vp, _vp, C.c_double,
                                       C.c_int, C.c_int, C.POINTER(SolveInfo), _vp]),
     "stag_gauge_force": (C.c_int, [_vp, C.c_double, _vp, _vp]),
@@ -114,6 +119,19 @@ _SIGS = {
     "stag_remez": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(Rational),
                              _dp]),
     "stag_apply_M_noalloc": (C.c_int, [C.POINTER(C.c_int), _vp, C.c_double, _vp, _vp, _vp]),
+    "stag_net_create": (C.c_int, [_vp, C.c_uint, C.POINTER(_vp)]),
+    "stag_net_destroy": (C.c_int, [_vp]),
+    "stag_ctx_set_net": (C.c_int, [_vp, _vp]),
+    "stag_net_nweights": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
+    "stag_net_get_weights": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_float)]),
+    "stag_net_set_weights": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_float)]),
+    "stag_net_get_grads": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_float)]),
+    "stag_net_apply": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "stag_net_loss_grad": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), _dp, _vp]),
+    "stag_net_train": (C.c_int, [_vp, C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.c_int, C.c_int,
+                                 C.c_double, _dp, _vp]),
+    "stag_fcg_solve": (C.c_int, [_vp, _vp, C.c_double, C.c_double, _vp, _vp, C.c_double, C.c_int,
+                                 C.POINTER(SolveInfo), _vp]),
 }
 
 
@@ -217,6 +235,13 @@ class Lattice:
         self._chk(lib().stag_ctx_device_bytes(self._h, C.byref(b)))
         return b.value
 
+    def autotune(self):
+        """Runs the hop autotuner; returns threads per block for FP64, FP32,
+        BF16 and float-float links."""
+        t = (C.c_int * 4)()
+        self._chk(lib().stag_autotune(self._h, t, _stream()))
+        return list(t)
+
     def launch_count(self):
         n = C.c_longlong(0)
         self._chk(lib().stag_ctx_launch_count(self._h, C.byref(n)))
@@ -280,6 +305,20 @@ class Lattice:
         self._chk(st)
         return sols, info
 
+    def multishift_solve_multi(self, mass, shifts, srcs, tol=1e-10, maxit=100000, mode=SOLVE_F64):
+        """Batched solve of len(srcs) systems with the same shifts; returns
+        (sols[r][k], infos[r])."""
+        n, ns = len(shifts), len(srcs)
+        sh = (C.c_double * n)(*[float(s) for s in shifts])
+        src_arr = (_vp * ns)(*[s.data_ptr() for s in srcs])
+        sols = [[self.vector() for _ in range(n)] for _ in range(ns)]
+        sol_arr = (_vp * (ns * n))(*[x.data_ptr() for row in sols for x in row])
+        infos = (SolveInfo * ns)()
+        st = lib().stag_multishift_solve_multi(self._h, mass, ns, n, sh, src_arr, sol_arr, tol, maxit,
+                                               mode, infos, _stream())
+        self._chk(st)
+        return sols, list(infos)
+
     def rational_apply(self, mass, rat, src, out=None, tol=1e-10, maxit=100000, mode=SOLVE_F64):
         r = Rational.make(*rat)
         out = self.vector() if out is None else out
@@ -326,9 +365,12 @@ class Lattice:
 
 def make_params(beta, mass, tau, nsteps, integrator, hb, act, force, npf=1, tol_md=1e-10,
                 tol_metro=1e-10, mode_md=SOLVE_F64, mode_metro=SOLVE_F64, seed=0, traj=0,
-                lam=OMELYAN_LAMBDA, maxit=100000, use_graphs=1):
-    """hb/act/force: (a0, a, b) partial fractions."""
+                lam=OMELYAN_LAMBDA, maxit=100000, use_graphs=1, ngauge=0, no_metropolis=0):
+    """hb/act/force: (a0, a, b) partial fractions; ngauge > 0: multi-step
+    integrator with ngauge gauge steps per position update."""
     p = Params()
+    p.ngauge = ngauge
+    p.no_metropolis = no_metropolis
     p.beta, p.mass, p.tau, p.nsteps, p.integrator, p.lam = beta, mass, tau, nsteps, integrator, lam
     p.npf = npf
     p.hb = Rational.make(*hb)
@@ -338,3 +380,85 @@ def make_params(beta, mass, tau, nsteps, integrator, hb, act, force, npf=1, tol_
     p.solve_mode_md, p.solve_mode_metro = mode_md, mode_metro
     p.maxit, p.seed, p.traj, p.use_graphs = maxit, seed, traj, use_graphs
     return p
+
+
+class Net:
+    """Learned gauge-covariant preconditioner bound to a Lattice (stag_net)."""
+
+    def __init__(self, lattice, seed=0):
+        self.lat = lattice
+        h = _vp()
+        st = lib().stag_net_create(lattice._h, seed, C.byref(h))
+        if st != OK:
+            raise StagError(st, lib().stag_last_error(lattice._h).decode())
+        self._h = h
+        self.nw = []
+        for layer in range(3):
+            n = C.c_int(0)
+            lib().stag_net_nweights(self._h, layer, C.byref(n))
+            self.nw.append(n.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().stag_net_destroy(self._h)
+            self._h = None
+
+    def attach(self):
+        """Makes this network the preconditioner of SOLVE_LEARNED on its lattice."""
+        self._chk(lib().stag_ctx_set_net(self.lat._h, self._h))
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        self.lat._chk(st)
+
+    def weights(self, layer):
+        a = np.zeros(2 * self.nw[layer], np.float32)
+        self._chk(lib().stag_net_get_weights(self._h, layer, a.ctypes.data_as(C.POINTER(C.c_float))))
+        return a.view(np.complex64).astype(np.complex128)
+
+    def set_weights(self, layer, w):
+        a = np.ascontiguousarray(np.asarray(w, np.complex64).reshape(-1))
+        assert a.size == self.nw[layer]
+        f = a.view(np.float32)
+        self._chk(lib().stag_net_set_weights(self._h, layer, f.ctypes.data_as(C.POINTER(C.c_float))))
+
+    def grads(self, layer):
+        a = np.zeros(2 * self.nw[layer], np.float32)
+        self._chk(lib().stag_net_get_grads(self._h, layer, a.ctypes.data_as(C.POINTER(C.c_float))))
+        return a.view(np.complex64).astype(np.complex128)
+
+    def apply(self, x_even, out_even=None):
+        out = self.lat.vector() if out_even is None else out_even
+        self._chk(lib().stag_net_apply(self._h, _ptr(x_even), _ptr(out), _stream()))
+        return out
+
+    def loss_grad(self, srcs, sols):
+        n = len(srcs)
+        a = (_vp * n)(*[s.data_ptr() for s in srcs])
+        b = (_vp * n)(*[s.data_ptr() for s in sols])
+        loss = C.c_double(0)
+        self._chk(lib().stag_net_loss_grad(self._h, n, a, b, C.byref(loss), _stream()))
+        return loss.value
+
+    def train(self, srcs, sols, epochs=1, batch=8, lr=1e-3):
+        n = len(srcs)
+        a = (_vp * n)(*[s.data_ptr() for s in srcs])
+        b = (_vp * n)(*[s.data_ptr() for s in sols])
+        loss = C.c_double(0)
+        self._chk(lib().stag_net_train(self._h, n, a, b, epochs, batch, lr, C.byref(loss), _stream()))
+        return loss.value
+
+
+def fcg_solve(lattice, net, mass, shift, src, tol=1e-10, maxit=100000):
+    """Flexible CG with the network as right preconditioner (net None: plain CG)."""
+    sol = lattice.vector()
+    info = SolveInfo()
+    st = lib().stag_fcg_solve(lattice._h, net._h if net is not None else None, mass, shift,
+                              _ptr(src), _ptr(sol), tol, maxit, C.byref(info), _stream())
+    lattice._chk(st)
+    return sol, info

@@ -122,6 +122,52 @@ def test_multishift_float_float_mode(S):
         assert rel(host(sols[k]), xo[k]) < 1e-8
 
 
+@pytest.mark.parametrize("mode", [0, 1, 3])
+def test_multishift_multi_system(S, mode):
+    """Batched solve of 5 systems (5 pseudofermion sources, two groups of the
+    multi-RHS hop) with the same shifts: each equals the oracle's own solve."""
+    dims, m = (6, 4, 6, 10), 0.05
+    U = synth.haar_links(dims, 25)
+    shifts = synth.log_shifts(6, 1e-4, 1.0)
+    srcs = [synth.gaussian_vector(dims, 30 + r) for r in range(5)]
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    tol = 1e-10
+    sols, infos = L.multishift_solve_multi(m, shifts, [dev(b) for b in srcs], tol=tol, mode=mode)
+    for r, b in enumerate(srcs):
+        xo, its, tot, st = O.multishift(dims, U, m, shifts, b, tol=1e-12)
+        assert infos[r].status == 0
+        if mode == 0:
+            # FP64: the same recursion as the oracle's, system by system
+            _, _, tot10, _ = O.multishift(dims, U, m, shifts, b, tol=tol)
+            assert abs(infos[r].iters - tot10) <= 2
+        for k in range(len(shifts)):
+            assert infos[r].true_resid[k] <= tol
+            x = host(sols[r][k])
+            assert rel(x, xo[k]) < 1e-7
+        rr = b - O.apply_M(dims, U, m, np.ascontiguousarray(host(sols[r][0]))) - shifts[0] * host(sols[r][0])
+        assert np.linalg.norm(rr) / np.linalg.norm(b) <= 1.01 * tol
+
+
+def test_autotuner_keeps_parity(S):
+    dims = (8, 8, 8, 8)
+    U = synth.haar_links(dims, 26)
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    tpb = L.autotune()
+    assert len(tpb) == 4 and all(t in (64, 128, 256) for t in tpb)
+    x = synth.gaussian_vector(dims, 27)
+    ref = O.dslash(dims, U, 1, x)
+    out = L.vector(S.PREC_F32)
+    L.apply_doe(dev(x, torch.complex64), out, S.PREC_F32)
+    assert rel(host(out), ref) < 2e-6
+    out = L.vector()
+    L.apply_doe(dev(x), out, S.PREC_F64FF)
+    assert rel(host(out), ref) < 1e-12
+    sols, info = L.multishift_solve(0.1, [0.0, 0.5], dev(x), tol=1e-10, mode=S.SOLVE_MIXED)
+    assert info.status == 0 and max(info.true_resid[:2]) <= 1e-10
+
+
 def test_M_ee_full_size_32x32x32x8(S):
     """The operator at the size of the 32^3x8 trajectory, checked in full."""
     dims = (32, 32, 32, 8)

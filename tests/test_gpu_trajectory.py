@@ -32,17 +32,18 @@ def _rats(rationals, key):
 
 
 def _run_both(S, rationals, dims, integrator, nsteps, tau, mode, seed_links=0, traj=0, beta=5.3,
-              mass=0.1, key="d8_1e-3"):
+              mass=0.1, key="d8_1e-3", ngauge=0, npf=1):
     hb, act = _rats(rationals, key)
     U = synth.near_unit_links(dims, 0.3, seed_links)
     po = O.make_params(beta, mass, tau, nsteps, integrator, hb, act, act, tol_md=1e-10,
-                       tol_metro=1e-10, seed=11, traj=traj)
+                       tol_metro=1e-10, seed=11, traj=traj, ngauge=ngauge, npf=npf)
     Uo, io, st = O.trajectory(dims, U, po)
     assert st == 0
     L = S.Lattice(dims)
     L.load_gauge(U)
     pg = S.make_params(beta, mass, tau, nsteps, integrator, hb, act, act, tol_md=1e-10,
-                       tol_metro=1e-10, mode_md=mode, mode_metro=mode, seed=11, traj=traj)
+                       tol_metro=1e-10, mode_md=mode, mode_metro=mode, seed=11, traj=traj,
+                       ngauge=ngauge, npf=npf)
     ig = L.md_trajectory(pg)
     return U, Uo, io, L.store_gauge(), ig
 
@@ -78,6 +79,29 @@ def test_trajectory_omelyan_rectangular(S, rationals, mode):
     assert ig["accepted"] == io["accepted"]
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_trajectory_two_pseudofermions(S, rationals, mode):
+    """N_pf = 2 (Sec. 2.1's multiple pseudofermions): the force solves both
+    pseudofermions in one batched multi-system solve."""
+    dims = (4, 4, 4, 4)
+    h, r = rationals["p+1/4_d6_1e-2"], rationals["p-1/2_d6_1e-2"]
+    hb, act = (h["a0"], h["a"], h["b"]), (r["a0"], r["a"], r["b"])
+    U = synth.near_unit_links(dims, 0.3, 9)
+    po = O.make_params(5.3, 0.2, 0.5, 4, 1, hb, act, act, npf=2, tol_md=1e-10, tol_metro=1e-10,
+                       seed=4, traj=2)
+    Uo, io, st = O.trajectory(dims, U, po)
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    pg = S.make_params(5.3, 0.2, 0.5, 4, 1, hb, act, act, npf=2, tol_md=1e-10, tol_metro=1e-10,
+                       mode_md=mode, mode_metro=mode, seed=4, traj=2)
+    ig = L.md_trajectory(pg)
+    # mixed mode: FP32 gauge force and, for N_pf > 1, the batched multi-system
+    # solver; the MD moves by ~2^-24 |F| per step and dH by ~1e-6 relative
+    tol = 1e-8 if mode == 0 else 5e-6 * max(1.0, abs(io["dH"]))
+    assert abs(ig["dH"] - io["dH"]) < tol
+    assert ig["accepted"] == io["accepted"]
+
+
 def test_trajectory_rejection_restores_links(S, rationals):
     """A far too coarse integrator (1 step, tau = 2) is rejected: links restored."""
     dims = (4, 4, 4, 4)
@@ -89,3 +113,47 @@ def test_trajectory_rejection_restores_links(S, rationals):
     info = L.md_trajectory(p)
     assert info["dH"] > 5 and not info["accepted"]
     np.testing.assert_allclose(L.store_gauge(), U, atol=2e-15)
+
+
+@pytest.mark.parametrize("integrator", [0, 1])
+def test_trajectory_multistep_f64(S, rationals, integrator):
+    """Multi-step scheme (gauge force on a finer time scale, 3 inner steps per
+    position update): FP64 dH and links as the oracle's."""
+    U, Uo, io, Ug, ig = _run_both(S, rationals, (4, 4, 4, 4), integrator, 4, 1.0, S.SOLVE_F64,
+                                  seed_links=2, traj=3, ngauge=3)
+    assert ig["n_force"] == io["n_force"] == (5 if integrator == 0 else 9)
+    assert abs(ig["dH"] - io["dH"]) < 1e-8
+    assert ig["accepted"] == io["accepted"]
+    assert np.abs(Ug - Uo).max() < 1e-9
+
+
+@pytest.mark.parametrize("integrator,nsteps", [(0, 40), (1, 8)])
+def test_trajectory_pure_gauge(S, rationals, integrator, nsteps):
+    """npf = 0: pure-gauge HMC (used to thermalise start configurations); an
+    accepted trajectory, so the moved links are compared."""
+    U, Uo, io, Ug, ig = _run_both(S, rationals, (6, 4, 6, 10), integrator, nsteps, 0.25, S.SOLVE_F64,
+                                  seed_links=4, traj=7, npf=0, beta=5.5)
+    assert ig["cg_iters"] == 0 and io["cg_iters"] == 0 and io["accepted"] == 1
+    assert abs(ig["dH"] - io["dH"]) < 1e-9
+    assert ig["accepted"] == io["accepted"]
+    assert np.abs(Ug - Uo).max() < 1e-11
+
+
+def test_no_metropolis_keeps_the_md_result(S, rationals):
+    """no_metropolis = 1 (thermalisation): a trajectory the oracle rejects is
+    kept, and the links are the oracle's molecular-dynamics result from the
+    same heatbath momenta."""
+    dims = (6, 4, 6, 10)
+    hb, act = _rats(rationals, "d8_1e-3")
+    U = synth.near_unit_links(dims, 0.3, 4)
+    po = O.make_params(5.5, 0.1, 1.0, 5, 1, hb, act, act, npf=0, seed=11, traj=7)
+    _, io, _ = O.trajectory(dims, U, po)
+    assert io["accepted"] == 0
+    W = O.momenta_heatbath(dims, 11, 7)
+    Um, _, _, _, st = O.md_integrate(dims, U, W, np.zeros((1, 3 * synth.volume(dims) // 2), complex), po)
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    ig = L.md_trajectory(S.make_params(5.5, 0.1, 1.0, 5, 1, hb, act, act, npf=0, seed=11, traj=7,
+                                       no_metropolis=1))
+    assert ig["accepted"] == 1 and abs(ig["dH"] - io["dH"]) < 1e-8
+    assert np.abs(L.store_gauge() - Um).max() < 1e-11
