@@ -48,7 +48,7 @@ def test_identity_weights_give_identity_network():
     for W in Ws:
         W[0, 0, 0] = 1.0
     b = synth.gaussian_vector(DIMS, 9)
-    y, _, _ = gcnn.network(DIMS, U, Ws, b)
+    y, _, _, _ = gcnn.network(DIMS, U, Ws, b)
     np.testing.assert_allclose(y, b, atol=1e-15)
 
 
@@ -74,3 +74,30 @@ def test_gradients_finite_difference():
                 fd = (lp - lm) / (2 * h)
                 an = grads[li][idx].real if part == "re" else grads[li][idx].imag
                 assert abs(fd - an) < 1e-6 * max(1.0, abs(an)), (li, idx, part, fd, an)
+
+
+def test_layer_adjoint_identity():
+    """<g, L phi> = <L^dag g, phi> for a layer with random complex weights."""
+    U = synth.haar_links(DIMS, 40)
+    V = synth.volume(DIMS)
+    W = _weights(41, 3, 2)
+    phis = _field(42, V, 2)
+    g = _field(43, V, 3)
+    y, _ = gcnn.layer_forward(DIMS, U, W, phis)
+    lhs = np.vdot(g, y)
+    rhs = np.vdot(gcnn.layer_adjoint(DIMS, U, W, g), phis)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_preconditioner_hermitian_positive():
+    """K = restrict A^dag A embed: <a, K b> = conj(<b, K a>) and <b, K b> = |A b|^2 >= 0."""
+    U = synth.haar_links(DIMS, 44)
+    Ws = [_weights(45, 4, 1), _weights(46, 4, 4), _weights(47, 1, 4)]
+    a = synth.gaussian_vector(DIMS, 48)
+    b = synth.gaussian_vector(DIMS, 49)
+    Ka, _, _, _ = gcnn.network(DIMS, U, Ws, a)
+    Kb, acts, _, _ = gcnn.network(DIMS, U, Ws, b)
+    assert abs(np.vdot(a, Kb) - np.conj(np.vdot(b, Ka))) < 1e-12 * abs(np.vdot(a, Kb))
+    bKb = np.vdot(b, Kb)
+    assert abs(bKb.imag) < 1e-12 * abs(bKb) and bKb.real > 0
+    assert abs(bKb.real - np.vdot(acts[-1], acts[-1]).real) < 1e-12 * bKb.real
