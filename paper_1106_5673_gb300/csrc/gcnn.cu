@@ -6,17 +6,20 @@
 //   (L phi)_o(n) = sum_i sum_t w[o][i][t] (T_t phi_i)(n),
 //   T_0 phi = phi(n), T_{1+mu} phi = U_mu(n) phi(n+mu),
 //   T_{5+mu} phi = U_mu(n-mu)^dag phi(n-mu),
-// which commutes with gauge transformations.  The network
-// K = restrict_even L3 L2 L1 embed_even (channels 1 -> H -> H -> 1) is linear;
-// it is trained to map sources b to solutions x of (M_ee + s) x = b by
-// minimising mean_j |K b_j - x_j|^2 / |x_j|^2 with Adam, using this file's
-// forward, adjoint (input gradient) and weight-gradient kernels.  Weights are
-// stored in BF16 for the forward pass (FP32 master copy for the optimiser);
-// arithmetic is FP32.  The flexible CG of this file (Golub-Ye's inexact
-// preconditioned CG) uses K as a right preconditioner for the lightest pole,
-// with FP64 vectors and the FP64-accurate float-float operator, so the
-// residual is judged in FP64 whatever K does.
-#include <math.h>
+// which commutes with gauge transformations.  A = L3 L2 L1 (channels
+// 1 -> H -> H -> 1); the preconditioner is K = restrict_even A^dag A
+// embed_even, Hermitian positive semi-definite by construction, where the
+// adjoint layer is (L^dag g)_i = sum_o sum_t conj(w[o][i][t]) T_t^dag g_o and
+// T_{1+mu}^dag = T_{5+mu}.  K is trained to map sources b to solutions x of
+// (M_ee + s) x = b by minimising mean_j |K b_j - x_j|^2 / |x_j|^2 with Adam,
+// using this file's forward, adjoint and weight-gradient kernels; the weight
+// gradient of a layer is 2 sum_n <T_t a_i(n), b_o(n)> with (a, b) = (layer
+// input, output gradient) for a forward layer and (output gradient, layer
+// input) for an adjoint layer.  Weights are stored in BF16 for the forward
+// pass (FP32 master copy for the optimiser); arithmetic is FP32.  The flexible
+// CG of this file (Golub-Ye's inexact preconditioned CG) uses K as a
+// preconditioner for the lightest pole, with FP64 vectors and the FP64-accurate
+// float-float operator, so the residual is judged in FP64 whatever K does.
 #include <stdlib.h>
 
 #include <vector>
@@ -35,8 +38,9 @@ struct stag_net {
     float2* w32[GC_NLAYER];            // FP32 master [cout][cin][9]
     __nv_bfloat162* w16[GC_NLAYER];    // BF16 copy used by the forward pass
     float2 *m[GC_NLAYER], *v[GC_NLAYER], *grad[GC_NLAYER];
-    float2* act[GC_NLAYER + 1];        // activations a0 [1][V][3] ... a3 [1][V][3]
-    float2* gact[GC_NLAYER + 1];       // gradients w.r.t. activations
+    float2* act[GC_NLAYER + 1];        // forward activations a0 [1][V][3], a1, a2 [H][V][3], a3 [1][V][3]
+    float2* cact[GC_NLAYER];           // adjoint activations c0 = A^dag A a0 [1], c1, c2 [H]
+    float2* gact[GC_NLAYER + 1];       // gradients (channels 1, H, H, 1), reused along the backward pass
     double* partials;                  // weight-gradient block partials
     double* dsc;                       // device scalars
     double* hsc;                       // pinned host scalars
@@ -321,6 +325,7 @@ int net_create(stag_ctx* ctx, unsigned seed, stag_net** out) {
     for (int l = 0; l <= GC_NLAYER; l++) {
         if (e == cudaSuccess) e = cudaMalloc(&net->act[l], sizeof(float2) * cs * chans[l]);
         if (e == cudaSuccess) e = cudaMalloc(&net->gact[l], sizeof(float2) * cs * chans[l]);
+        if (l < GC_NLAYER && e == cudaSuccess) e = cudaMalloc(&net->cact[l], sizeof(float2) * cs * chans[l]);
     }
     if (e == cudaSuccess)
         e = cudaMalloc(&net->partials, sizeof(double) * 2 * GC_H * GC_H * GC_TAPS * (size_t)net->nblk);
@@ -372,6 +377,7 @@ void net_destroy(stag_net* net) {
     for (int l = 0; l <= GC_NLAYER; l++) {
         cudaFree(net->act[l]);
         cudaFree(net->gact[l]);
+        if (l < GC_NLAYER) cudaFree(net->cact[l]);
     }
     cudaFree(net->partials);
     cudaFree(net->dsc);
@@ -379,23 +385,34 @@ void net_destroy(stag_net* net) {
     delete net;
 }
 
-// z = K b (FP64 even-site vectors in and out)
-int net_apply(stag_net* net, const double2* b, double2* z, cudaStream_t s) {
+// forward activations a_l and adjoint activations c_l of K b
+static void net_forward(stag_net* net, const double2* b, cudaStream_t s) {
     stag_ctx* ctx = net->ctx;
     k_gc_embed<<<nblocks(ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, b, net->act[0]);
+    ctx->nlaunch++;
     for (int l = 0; l < GC_NLAYER; l++) layer_launch(net, l, net->act[l], net->act[l + 1], 0, s);
-    k_gc_restrict<<<nblocks(ctx->g.Vh, TPB), TPB, 0, s>>>(ctx->g, net->act[GC_NLAYER], z);
-    ctx->nlaunch += 2;
+    for (int l = GC_NLAYER - 1; l >= 0; l--)
+        layer_launch(net, l, l == GC_NLAYER - 1 ? net->act[GC_NLAYER] : net->cact[l + 1], net->cact[l], 1, s);
+}
+
+// z = K b = restrict A^dag A embed b (FP64 even-site vectors in and out)
+int net_apply(stag_net* net, const double2* b, double2* z, cudaStream_t s) {
+    stag_ctx* ctx = net->ctx;
+    net_forward(net, b, s);
+    k_gc_restrict<<<nblocks(ctx->g.Vh, TPB), TPB, 0, s>>>(ctx->g, net->cact[0], z);
+    ctx->nlaunch++;
     STAG_LAUNCH_CHECK(ctx, "net apply");
     return STAG_OK;
 }
 
 // loss and weight gradients (accumulated into grad[]) of the pairs (b_j, x_j);
-// returns the mean loss in *loss
+// returns the mean loss in *loss.  Back-propagation: through the adjoint
+// layers (L0^dag applied last, so first here), then the forward layers.
 int net_loss_grad(stag_net* net, int npairs, const double2* const* bs, const double2* const* xs, double* loss,
                   cudaStream_t s) {
     stag_ctx* ctx = net->ctx;
     STAG_CUDA(ctx, cudaMemsetAsync(net->dsc, 0, sizeof(double) * 2, s));
+    float2** g = net->gact;
     for (int j = 0; j < npairs; j++) {
         // |x|^2
         int st = blas_dot_re(ctx, STAG_PREC_F64, xs[j], xs[j], net->dsc + 2, s);
@@ -403,15 +420,21 @@ int net_loss_grad(stag_net* net, int npairs, const double2* const* bs, const dou
         STAG_CUDA(ctx, cudaMemcpyAsync(net->hsc + 2, net->dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
         STAG_CUDA(ctx, cudaStreamSynchronize(s));
         const double inv = 1.0 / (net->hsc[2] * npairs);
-        k_gc_embed<<<nblocks(ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, bs[j], net->act[0]);
-        for (int l = 0; l < GC_NLAYER; l++) layer_launch(net, l, net->act[l], net->act[l + 1], 0, s);
-        k_gc_lossgrad<<<nblocks(ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, net->act[GC_NLAYER], xs[j], inv,
-                                                             net->gact[GC_NLAYER], net->dsc);
-        for (int l = GC_NLAYER - 1; l >= 0; l--) {
-            wgrad_launch(net, l, net->act[l], net->gact[l + 1], j > 0, s);
-            if (l > 0) layer_launch(net, l, net->gact[l + 1], net->gact[l], 1, s);
+        net_forward(net, bs[j], s);
+        // g[0] = dloss/dconj(c0) (even sites), loss partial sums
+        k_gc_lossgrad<<<nblocks(ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, net->cact[0], xs[j], inv, g[0], net->dsc);
+        ctx->nlaunch++;
+        // adjoint layer l: c_l = L_l^dag c_{l+1}; gradient at c_l is g[l]
+        for (int l = 0; l < GC_NLAYER; l++) {
+            const float2* cin = (l == GC_NLAYER - 1) ? net->act[GC_NLAYER] : net->cact[l + 1];
+            wgrad_launch(net, l, g[l], cin, j > 0, s);
+            layer_launch(net, l, g[l], g[l + 1], 0, s);  // gradient at c_{l+1}; g[3] is the one at a3
         }
-        ctx->nlaunch += 2;
+        // forward layer l: a_{l+1} = L_l a_l; gradient at a_{l+1} is g[l + 1]
+        for (int l = GC_NLAYER - 1; l >= 0; l--) {
+            wgrad_launch(net, l, net->act[l], g[l + 1], 1, s);
+            if (l > 0) layer_launch(net, l, g[l + 1], g[l], 1, s);
+        }
         STAG_LAUNCH_CHECK(ctx, "net gradient");
     }
     STAG_CUDA(ctx, cudaMemcpyAsync(net->hsc, net->dsc, sizeof(double), cudaMemcpyDeviceToHost, s));

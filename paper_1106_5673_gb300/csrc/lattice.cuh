@@ -385,6 +385,42 @@ template <int N> STAG_D void block_sum_n(double v[N]) {
     }
 }
 
+STAG_D float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sums of N <= 32 per-thread values of type T: returns the sum of
+// series j in lane j of warp 0 (j < N; other threads get 0).  The warp level
+// runs in T (for FP32 data: FP32 shuffles, since GB300 executes FP64 at a
+// small fraction of its FP32 rate), the cross-warp level in FP64, one lane per
+// series adding the warps' partials in order.
+template <int N, typename T> STAG_D double block_sum_nv(const T v[N]) {
+    static_assert(N <= 32, "one lane per series");
+    __shared__ double red_v[32][N];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    T s[N];
+#pragma unroll
+    for (int j = 0; j < N; j++) s[j] = v[j];
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        if constexpr (sizeof(T) == 4) s[j] = warp_sum_f(s[j]);
+        else s[j] = warp_sum(s[j]);
+    }
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < N; j++) red_v[w][j] = (double)s[j];
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x < N) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int i = 0; i < nw; i++) out += red_v[i][threadIdx.x];
+    }
+    return out;
+}
+
 // In the last block: out[s] = sum_i partials[s * nb + i] for s < nseries,
 // one warp per series (all warps in parallel).  Ends with a barrier.
 STAG_D void reduce_series(const double* partials, int nseries, int nb, double* out_shared) {
@@ -405,8 +441,9 @@ STAG_D void reduce_series(const double* partials, int nseries, int nb, double* o
 // Level 1: the last block to finish among the gridDim.y x STAG_RED_GROUP
 // blocks of each column group sums that group's columns into
 // gpart[s * ngroups + group]; level 2: the last group to finish sums gpart.
-// One L2 round trip of 32 loads per series at each level instead of a serial
-// sweep over all partials.  Returns true in exactly one block, whose
+// At each level one thread per series adds at most STAG_RED_GROUP (level 1)
+// or ngroups (level 2) values, so the serial tail is short and uses few FP64
+// operations (GB300 executes FP64 at a small fraction of its FP32 rate).  Returns true in exactly one block, whose
 // out_shared[0..nseries) then holds the sums; counters[0] and
 // counters[1 + group] return to zero.
 #define STAG_RED_GROUP 32
@@ -426,10 +463,20 @@ STAG_D bool grid_reduce_series(const double* partials, double* gpart, unsigned i
     __syncthreads();
     if (!s_last) return false;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int sidx = w; sidx < nseries; sidx += nw) {
-        double v = (lane < gsz) ? __ldcg(partials + (size_t)sidx * nbx + g0 + lane) : 0.0;
-        v = warp_sum(v);
-        if (lane == 0) gpart[(size_t)sidx * ngr + grp] = v;
+    if (nseries <= nw) {  // level 1, few series: one warp per series, one load per lane
+        if (w < nseries) {
+            double v = (lane < gsz) ? __ldcg(partials + (size_t)w * nbx + g0 + lane) : 0.0;
+            v = warp_sum(v);
+            if (lane == 0) gpart[(size_t)w * ngr + grp] = v;
+        }
+    } else {  // level 1, many series: one thread per series, columns in order
+        for (int sidx = threadIdx.x; sidx < nseries; sidx += blockDim.x) {
+            const double* src = partials + (size_t)sidx * nbx + g0;
+            double v = 0.0;
+#pragma unroll 8
+            for (int i = 0; i < gsz; i++) v += __ldcg(src + i);
+            gpart[(size_t)sidx * ngr + grp] = v;
+        }
     }
     __threadfence();
     __syncthreads();
@@ -440,11 +487,21 @@ STAG_D bool grid_reduce_series(const double* partials, double* gpart, unsigned i
     }
     __syncthreads();
     if (!s_last) return false;
-    for (int sidx = w; sidx < nseries; sidx += nw) {
-        double v = 0.0;
-        for (int i = lane; i < ngr; i += 32) v += __ldcg(gpart + (size_t)sidx * ngr + i);
-        v = warp_sum(v);
-        if (lane == 0) out_shared[sidx] = v;
+    if (nseries <= nw) {  // level 2 as level 1
+        if (w < nseries) {
+            double v = 0.0;
+            for (int i = lane; i < ngr; i += 32) v += __ldcg(gpart + (size_t)w * ngr + i);
+            v = warp_sum(v);
+            if (lane == 0) out_shared[w] = v;
+        }
+    } else {
+        for (int sidx = threadIdx.x; sidx < nseries; sidx += blockDim.x) {
+            const double* src = gpart + (size_t)sidx * ngr;
+            double v = 0.0;
+#pragma unroll 8
+            for (int i = 0; i < ngr; i++) v += __ldcg(src + i);
+            out_shared[sidx] = v;
+        }
     }
     __syncthreads();
     return true;

@@ -13,57 +13,70 @@
 //       (zeta^{j-1} a_{j-1} (1 + d_k a_j) + a_j b_{j-1} (zeta^{j-1} - zeta^j)),
 //   a_k = alpha zeta^{j+1}/zeta^j,  b_k = beta (zeta^{j+1}/zeta^j)^2,
 // shift k stays active while |zeta_k|^2 |r_new|^2 > tol^2 |b|^2.  Called by
-// every thread of one block (one thread per shift); thread 0 writes the
-// system's scalars.
+// every thread of one block (one thread per shift).  Every value of the state
+// is loaded once, up front and in parallel, and written once at the end: this
+// runs in the single block that finishes last, while the rest of the GPU
+// waits, so its cost is its chain of dependent global-memory round trips.
 STAG_D void ms_scalar_update(MSState* st, double t0, double t1, double t2, double t3) {
     __shared__ double s_alpha, s_beta, s_rr;
     __shared__ int s_iter;
-    if (threadIdx.x == 0) {
+    const int k = threadIdx.x;
+    const int n = st->n, base = st->base;
+    const double ao = st->alpha_old, bo = st->beta_old, tol2 = st->tol2bb, sb = st->shifts[base];
+    int actk = 0;
+    double zo = 0.0, z = 1.0, sh = 0.0;
+    if (k < n) {
+        actk = st->active[k];
+        zo = st->zeta_old[k];
+        z = st->zeta[k];
+        sh = st->shifts[k];
+    }
+    if (k == 0) {
+        const int it = st->iter;
         const double alpha = t3 / t0;
         double rr_new = t3 - 2.0 * alpha * t1 + alpha * alpha * t2;
         if (rr_new < 0.0) rr_new = 0.0;
         s_alpha = alpha;
         s_rr = rr_new;
         s_beta = rr_new / t3;
-        s_iter = st->iter + 1;
-        st->pw = t0;
-        st->alpha = alpha;
+        s_iter = it + 1;
     }
     __syncthreads();
-    const int k = threadIdx.x;
+    const double alpha = s_alpha, beta = s_beta, rr_new = s_rr;
+    const int iter = s_iter;
     int act = 0;
-    if (k < st->n) {
-        if (st->active[k]) {
-            const double alpha = s_alpha;
-            const double d = st->shifts[k] - st->shifts[st->base];
-            const double zo = st->zeta_old[k], z = st->zeta[k], ao = st->alpha_old;
-            const double den = zo * ao * (1.0 + d * alpha) + alpha * st->beta_old * (zo - z);
+    if (k < n) {
+        if (actk) {
+            const double d = sh - sb;
+            const double den = zo * ao * (1.0 + d * alpha) + alpha * bo * (zo - z);
             const double zn = z * zo * ao / den;
             const double ratio = zn / z;
             st->ak[k] = alpha * ratio;
-            st->bk[k] = s_beta * ratio * ratio;
+            st->bk[k] = beta * ratio * ratio;
             st->zeta_old[k] = z;
             st->zeta[k] = zn;
             st->upd_x[k] = 1;
-            st->iters_shift[k] = s_iter;
-            st->active[k] = (zn * zn * s_rr > st->tol2bb) ? 1 : 0;
+            st->iters_shift[k] = iter;
+            act = (zn * zn * rr_new > tol2) ? 1 : 0;
+            st->active[k] = act;
         } else {
             st->upd_x[k] = 0;
             st->ak[k] = 0.0;
         }
-        act = st->active[k];
     }
     const int n_active = __syncthreads_count(act);
-    if (threadIdx.x == 0) {
-        st->iter = s_iter;
+    if (k == 0) {
+        st->pw = t0;
+        st->alpha = alpha;
+        st->iter = iter;
         st->n_active = n_active;
-        st->beta = s_beta;
-        st->rr = s_rr;
-        st->alpha_old = s_alpha;
-        st->beta_old = s_beta;
-        const int bad = !isfinite(s_rr) || !isfinite(s_beta) || !isfinite(s_alpha);
+        st->beta = beta;
+        st->rr = rr_new;
+        st->alpha_old = alpha;
+        st->beta_old = beta;
+        const int bad = !isfinite(rr_new) || !isfinite(beta) || !isfinite(alpha);
         if (bad) st->nonfinite = 1;
-        st->stop_next = (n_active == 0 || s_iter >= st->maxit || bad) ? 1 : 0;
+        st->stop_next = (n_active == 0 || iter >= st->maxit || bad) ? 1 : 0;
     }
 }
 

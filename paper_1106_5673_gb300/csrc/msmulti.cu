@@ -89,9 +89,9 @@ __global__ void __launch_bounds__(256) k_mm_B3(Geom g, Links U, const typename V
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     int js[NRM];
     const int nj = group_systems(st, nsys, js);
-    double flat[NRM * 4];
+    R flat[NRM * 4];
 #pragma unroll
-    for (int i = 0; i < NRM * 4; i++) flat[i] = 0.0;
+    for (int i = 0; i < NRM * 4; i++) flat[i] = 0;
     if (h < g.Vh && nj > 0) {
         Vec3<R> acc[NRM];
         hops<R, LP>(g, U, T, vstride, js, nj, h, 0, acc);
@@ -118,14 +118,12 @@ __global__ void __launch_bounds__(256) k_mm_B3(Geom g, Links U, const typename V
             }
         }
     }
-    block_sum_n<NRM * 4>(flat);
+    const double bsum = block_sum_nv<NRM * 4, R>(flat);
     const size_t nbx = gridDim.x;
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int q = 0; q < NRM; q++)
-            if (q < nj)
-#pragma unroll
-                for (int j = 0; j < 4; j++) partials[((size_t)js[q] * 4 + j) * nbx + blockIdx.x] = flat[4 * q + j];
+    if (threadIdx.x < 4 * nj) {
+        const int q = threadIdx.x >> 2, j = threadIdx.x & 3;
+        partials[((size_t)js[q] * 4 + j) * nbx + blockIdx.x] = bsum;
+    }
     __shared__ double s_sum[STAG_MAXRHS * 4];
     if (grid_reduce_series(partials, gpart, counter, nsys * 4, s_sum)) {
         for (int r = 0; r < nsys; r++)

@@ -217,9 +217,9 @@ __global__ void __launch_bounds__(256) k_b_B3(Geom g, const void* __restrict__ U
     int js[NR];
 #pragma unroll
     for (int q = 0; q < NR; q++) js[q] = (q < nj) ? st->act[q0 + q] : 0;
-    double sums[NR][4];
+    float flat[NR * 4];
 #pragma unroll
-    for (int q = 0; q < NR; q++) sums[q][0] = sums[q][1] = sums[q][2] = sums[q][3] = 0.0;
+    for (int q = 0; q < NR * 4; q++) flat[q] = 0.f;
     if (h < g.Vh && nj > 0) {
         const Site s = site_of(g, h, 0);
         Vec3<float> acc[NR];
@@ -240,33 +240,30 @@ __global__ void __launch_bounds__(256) k_b_B3(Geom g, const void* __restrict__ U
                     e += rv.c[i].re * rv.c[i].re + rv.c[i].im * rv.c[i].im;
                 }
                 st_vec(W + js[q] * stride, h, w);
-                sums[q][0] = a;
-                sums[q][1] = b;
-                sums[q][2] = d;
-                sums[q][3] = e;
+                flat[q * 4 + 0] = a;
+                flat[q * 4 + 1] = b;
+                flat[q * 4 + 2] = d;
+                flat[q * 4 + 3] = e;
             }
         }
     }
     const size_t nbx = gridDim.x;
-    double flat[NR * 4];
-#pragma unroll
-    for (int q = 0; q < NR; q++)
-#pragma unroll
-        for (int j = 0; j < 4; j++) flat[q * 4 + j] = sums[q][j];
-    block_sum_n<NR * 4>(flat);
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int q = 0; q < NR; q++)
-            if (q < nj)
-#pragma unroll
-                for (int j = 0; j < 4; j++) partials[((size_t)(q0 + q) * 4 + j) * nbx + blockIdx.x] = flat[q * 4 + j];
+    if (nj > 0) {  // rows past the active right-hand sides only join the grid reduction
+        const double bsum = block_sum_nv<NR * 4, float>(flat);
+        if (threadIdx.x < 4 * nj) partials[((size_t)q0 * 4 + threadIdx.x) * nbx + blockIdx.x] = bsum;
+    }
     __shared__ double s_sum[STAG_MAXSHIFT][4];
     if (grid_reduce_series(partials, gpart, counter, nact * 4, &s_sum[0][0])) {
-        if (threadIdx.x == 0) {
-            int keep = 0, bad = 0, capped = 0;
-            for (int a = 0; a < nact; a++) {
-                const int k = st->act[a];
-                st->uact[a] = k;
+        // one lane of warp 0 per active right-hand side (nact <= 32), all state
+        // loaded up front; the still-active list is compacted in order by a ballot
+        if (threadIdx.x < 32) {
+            const int a = threadIdx.x;
+            const int maxit = st->maxit;
+            int k = 0, keep = 0, bad = 0, capped = 0;
+            if (a < nact) {
+                k = st->act[a];
+                const int it = st->iter[k] + 1;
+                const double tol2 = st->tol2bb[k];
                 const double rr = s_sum[a][3];  // fresh |r_k|^2 of this iteration
                 const double alpha = rr / s_sum[a][0];
                 double rr_new = rr - 2.0 * alpha * s_sum[a][1] + alpha * alpha * s_sum[a][2];
@@ -275,18 +272,25 @@ __global__ void __launch_bounds__(256) k_b_B3(Geom g, const void* __restrict__ U
                 st->beta[k] = rr_new / rr;
                 st->rr_prev[k] = rr;
                 st->rr[k] = rr_new;
-                st->iter[k] += 1;
-                if (!isfinite(rr_new) || !isfinite(alpha)) bad = 1;
-                if (st->iter[k] >= st->maxit) capped = 1;
-                if (rr_new <= st->tol2bb[k])
+                st->iter[k] = it;
+                st->uact[a] = k;
+                bad = !isfinite(rr_new) || !isfinite(alpha);
+                capped = it >= maxit;
+                if (rr_new <= tol2)
                     st->want_rel[k] = 1;  // parked until the host checks it
                 else
-                    st->act[keep++] = k;
+                    keep = 1;
             }
-            st->n_uact = nact;
-            st->n_act = keep;
-            if (bad) st->nonfinite = 1;
-            st->stop_next = (keep == 0 || bad || capped) ? 1 : 0;
+            const unsigned int m = __ballot_sync(0xffffffffu, keep);
+            if (keep) st->act[__popc(m & ((1u << a) - 1u))] = k;
+            const int anybad = __any_sync(0xffffffffu, bad), anycap = __any_sync(0xffffffffu, capped);
+            if (a == 0) {
+                const int nkeep = __popc(m);
+                st->n_uact = nact;
+                st->n_act = nkeep;
+                if (anybad) st->nonfinite = 1;
+                st->stop_next = (nkeep == 0 || anybad || anycap) ? 1 : 0;
+            }
         }
     }
 }

@@ -142,34 +142,25 @@ __global__ void __launch_bounds__(256) k_ms_B3(Geom g, Links U, const typename V
                                                    double* gpart, unsigned int* counter) {
     if (!st->live) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
-    double pw = 0.0, rw = 0.0, ww = 0.0, rr = 0.0;
+    R sv[4] = {0, 0, 0, 0};
     if (h < g.Vh) {
         const Site s = site_of(g, h, 0);
         const Vec3<R> acc = hopL<R, LP>(g, U, t, h, 0, s);
         const Vec3<R> pv = load_vec(p, h), rv = load_vec(r, h);
         const R c0 = (R)st->c0;
         Vec3<R> wv;
-        R a = 0, b = 0, c = 0, d = 0;
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             wv.c[i] = c0 * pv.c[i] - (R)0.5 * acc.c[i];
-            a += pv.c[i].re * wv.c[i].re + pv.c[i].im * wv.c[i].im;
-            b += rv.c[i].re * wv.c[i].re + rv.c[i].im * wv.c[i].im;
-            c += wv.c[i].re * wv.c[i].re + wv.c[i].im * wv.c[i].im;
-            d += rv.c[i].re * rv.c[i].re + rv.c[i].im * rv.c[i].im;
+            sv[0] += pv.c[i].re * wv.c[i].re + pv.c[i].im * wv.c[i].im;
+            sv[1] += rv.c[i].re * wv.c[i].re + rv.c[i].im * wv.c[i].im;
+            sv[2] += wv.c[i].re * wv.c[i].re + wv.c[i].im * wv.c[i].im;
+            sv[3] += rv.c[i].re * rv.c[i].re + rv.c[i].im * rv.c[i].im;
         }
         st_vec(w, h, wv);
-        pw = (double)a;
-        rw = (double)b;
-        ww = (double)c;
-        rr = (double)d;
     }
-    double v[4] = {pw, rw, ww, rr};
-    block_sum_n<4>(v);
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int j = 0; j < 4; j++) partials[j * gridDim.x + blockIdx.x] = v[j];
-    }
+    const double bsum = block_sum_nv<4, R>(sv);
+    if (threadIdx.x < 4) partials[threadIdx.x * gridDim.x + blockIdx.x] = bsum;
     __shared__ double s_t[4];
     if (grid_reduce_series(partials, gpart, counter, 4, s_t)) ms_scalar_update(st, s_t[0], s_t[1], s_t[2], s_t[3]);
 }

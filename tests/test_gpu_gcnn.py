@@ -78,7 +78,7 @@ def test_network_forward(S, dims):
     net, Wq = make_net(S, L, random_weights(4))
     b = synth.gaussian_vector(dims, 5)
     y = host(net.apply(dev(b)))
-    ref, _, _ = G.network(dims, U, Wq, b)
+    ref, _, _, _ = G.network(dims, U, Wq, b)
     assert rel(y, ref) < 1e-5
     # BF16 weights really are the ones used: the FP32 master weights differ
     Wm = [net.weights(l).reshape(SHAPES_W[l]) for l in range(3)]
