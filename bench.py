@@ -34,6 +34,11 @@ DIMS = (32, 32, 32, 8)
 BETA, MASS, TAU, NSTEPS, DEG, LO, HI, TOL = 5.5, 0.0075, 1.0, 20, 15, 1e-5, 64.0, 1e-10
 ROOF_DIMS = (64, 64, 64, 16)  # working set >= 4x L2 for the Dslash roofline
 THERM, THERM_STEPS = 60, 40   # pure-gauge thermalisation: trajectories, Omelyan steps (tau = 1)
+# DRAM bytes (read + write) per output site of k_hop<float,1> from one ncu
+# capture at 48^3x16 (profiles/k_hop_f32_48x48x48x16.md): 383.8 MB / 884736
+# sites; traffic grows in proportion to the sites, so it is scaled to the
+# roofline lattice by Vh.  Algorithmic bytes per site: 600.
+HOP_TRAFFIC_PER_SITE = 433.8
 # total multi-shift iterations of one FP64 trajectory of this workload, as
 # counted by the library's FP64 path (identical to the oracle's recursion);
 # used to scale the oracle's per-iteration cost to a trajectory
@@ -147,6 +152,49 @@ def thermalise(stag, L, rat, seed, ntraj=THERM):
     return info["plaq"] if info else None
 
 
+def kernel_table(stag, torch, L, params, path, top=14):
+    """Per-kernel device time of one trajectory from CUPTI (torch.profiler):
+    launches, total, share and average per kernel name; written to `path` and
+    summarised (top kernels) in the JSON line."""
+    from torch.profiler import ProfilerActivity, profile
+    torch.cuda.synchronize()
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        info = L.md_trajectory(params)
+        torch.cuda.synchronize()
+    rows = []
+    for e in prof.key_averages():
+        t = getattr(e, "device_time_total", None)
+        if t is None:
+            t = e.cuda_time_total
+        if t > 0:
+            rows.append((e.key, e.count, t))
+    tot = sum(r[2] for r in rows)
+    rows.sort(key=lambda r: -r[2])
+    with open(path, "w") as f:
+        f.write("# one trajectory (cg_iters %d, t_total %.3f s): kernel, launches, total_ms, share, avg_us\n"
+                % (info["cg_iters"], info["t_total"]))
+        for k, c, t in rows:
+            f.write("%s\t%d\t%.3f\t%.4f\t%.3f\n" % (k, c, t / 1e3, t / tot, t / c))
+    return {"source": "CUPTI via torch.profiler, one untimed trajectory after the timed region",
+            "total_ms": tot / 1e3, "launches": sum(r[1] for r in rows),
+            "top": [{"kernel": _kernel_name(k), "launches": c, "ms": t / 1e3, "share": t / tot,
+                     "avg_us": t / c} for k, c, t in rows[:top]]}
+
+
+def _kernel_name(k):
+    """Kernel name without namespace prefix and argument list."""
+    k = k.replace("(anonymous namespace)::", "")
+    if k.startswith("void "):
+        k = k[5:]
+    depth, out = 0, []
+    for ch in k:
+        depth += (ch == "<") - (ch == ">")
+        if ch == "(" and depth == 0:
+            break
+        out.append(ch)
+    return "".join(out)
+
+
 def cpu_sample(U, rat_act, iters_per_traj, n_force):
     """The FP64 oracle on the host: a bounded sample of the trajectory's work,
     scaled to seconds per trajectory."""
@@ -220,7 +268,9 @@ def main():
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
-    ap.add_argument("--ref-iters", type=int, default=50000)
+    ap.add_argument("--ref-iters", type=int, default=137500,
+                    help="FP64 multi-shift iterations per trajectory used to scale the oracle sample "
+                         "(the library's FP64 count on the thermalised start)")
     ap.add_argument("--mode", default="mixed", choices=["mixed", "f64", "ff", "bf16"],
                     help="solver mode of the timed trajectories")
     ap.add_argument("--nsteps", type=int, default=NSTEPS,
@@ -236,6 +286,9 @@ def main():
     ap.add_argument("--profile-window", action="store_true",
                     help="bracket the first timed trajectory with cudaProfilerStart/Stop "
                          "(for ncu --profile-from-start off)")
+    ap.add_argument("--kernel-table", default=None, metavar="FILE",
+                    help="after the timed region, record one more trajectory with CUPTI "
+                         "(torch.profiler) and write its per-kernel device-time table to FILE")
     ap.add_argument("--with-ff", action="store_true",
                     help="also run the float-float FP64 form in the same-start comparison")
     args = ap.parse_args()
@@ -345,6 +398,10 @@ def main():
         roof = hop_roofline(stag, torch, DIMS)
         roof_large = hop_roofline(stag, torch, ROOF_DIMS)
     peak, peak_kind = _peaks()
+    ktable = None
+    if args.kernel_table:
+        ktable = kernel_table(stag, torch, L, _params(stag, rat_hb, rat_act, mode, 998, 100 + rank),
+                              args.kernel_table)
 
     line = {
         "metric": _metric(), "value": value, "unit": "s/trajectory", "n_gpus": world,
@@ -361,15 +418,22 @@ def main():
                                                "steps, no Metropolis)" % (args.therm, THERM_STEPS),
                              "plaquette": plaq_start},
                    "l2": "working set > L2 (links fp64+fp32+bf16 ~176 MB, solver vectors ~200 MB)"},
-        "roofline": None if roof is None else {
-            "bound": "hbm", "achieved": roof["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": roof["gbs"] / peak, "traffic": None,
-            "kernel": "k_hop<float,LP32> (D_oe, FP32 12-real links)",
-            "dims": roof["dims"], "peak_kind": peak_kind},
-        "roofline_large": None if roof_large is None else {
+        # the FP32 even/odd hop that the solver kernels (k_ms_A/B3, k_b_A/B3)
+        # share, on the roofline lattice (working set > 4x L2); algorithmic
+        # bytes 600 per output site, traffic from the ncu capture
+        "roofline": None if roof_large is None else {
             "bound": "hbm", "achieved": roof_large["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": roof_large["gbs"] / peak, "dims": roof_large["dims"],
-            "gflops": roof_large["gflops"]},
+            "frac": roof_large["gbs"] / peak,
+            "traffic": HOP_TRAFFIC_PER_SITE * roof_large["bytes"] / 600.0,
+            "kernel": "k_hop<float,1> (D_oe, FP32 12-real links)", "dims": roof_large["dims"],
+            "seconds_per_launch": roof_large["seconds"], "algorithmic_bytes": roof_large["bytes"],
+            "dram_gbs": HOP_TRAFFIC_PER_SITE * roof_large["bytes"] / 600.0 / roof_large["seconds"] / 1e9,
+            "gflops": roof_large["gflops"], "peak_kind": peak_kind},
+        # the same kernel on the workload's lattice (its links fit in L2)
+        "roofline_workload": None if roof is None else {
+            "bound": "hbm", "achieved": roof["gbs"], "peak": peak, "unit": "GB/s",
+            "frac": roof["gbs"] / peak, "dims": roof["dims"], "seconds_per_launch": roof["seconds"],
+            "gflops": roof["gflops"]},
         "e2e": None if t_e2e is None else {
             "value": t_e2e, "unit": "s/trajectory", "h2d_bytes_per_step": link_bytes,
             "d2h_bytes_per_step": link_bytes},
@@ -380,6 +444,7 @@ def main():
         "mode": args.mode,
         "cg_iters_per_traj": iters_timed,
         "compare_same_start": compare,
+        "kernel_table": ktable,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = compare["f64"]["cg_iters"] if compare else (REF_ITERS_PER_TRAJ or args.ref_iters)

@@ -44,8 +44,15 @@ STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
 
 template <int LP>
 __global__ void __launch_bounds__(256) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
-                                                 float2* __restrict__ T, size_t stride, const BCGState* st) {
-    if (!st->live) return;
+                                                 float2* __restrict__ T, size_t stride, BCGState* st) {
+    // a stop requested by the previous iteration takes effect here, after that
+    // iteration's vector update
+    const int live = st->live, stop = st->stop_next;
+    if (!live) return;
+    if (stop) {
+        if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->live = 0;
+        return;
+    }
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     const int q0 = blockIdx.y * NR, nact = st->n_act;
     if (h >= g.Vh || q0 >= nact) return;
@@ -322,9 +329,6 @@ __global__ void k_b_CD(long n, size_t stride, float2* __restrict__ R, const floa
                 p[i] = pv;
             }
         }
-    }
-    if (last_block_n(counter, gridDim.x * gridDim.y)) {
-        if (threadIdx.x == 0 && st->stop_next) st->live = 0;
     }
 }
 

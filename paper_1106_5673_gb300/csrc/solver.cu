@@ -54,8 +54,15 @@ static Links make_links(const stag_ctx* ctx, int lp) {
 template <typename R, int LP>
 __global__ void __launch_bounds__(256) k_ms_A(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ p,
-                                                  typename VT<R>::T* __restrict__ t, const int* live) {
-    if (!*live) return;
+                                                  typename VT<R>::T* __restrict__ t, MSState* st) {
+    // the stop requested by the previous iteration's scalar update takes
+    // effect here, after that iteration's vector update has run
+    const int live = st->live, stop = st->stop_next;
+    if (!live) return;
+    if (stop) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->live = 0;
+        return;
+    }
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= g.Vh) return;
     const Site s = site_of(g, h, 1);
@@ -172,9 +179,6 @@ __global__ void k_ms_CD(long n, long stride, V2* __restrict__ r, const V2* __res
     if (!st->live) return;
     ms_vector_update<V2, R>(n, stride, blockIdx.x * (long)blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x, r,
                             w, p, pk, xk, st);
-    if (last_block(counter)) {
-        if (threadIdx.x == 0 && st->stop_next) st->live = 0;
-    }
 }
 
 template <typename V2, typename R>
@@ -485,7 +489,7 @@ void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
     const int tpb = hop_tpb(ctx, LP);
     const int nb_hop = nblocks(g.Vh, tpb);
     const int nb_blas = ctx->num_sms * 4;
-    k_ms_A<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, &ctx->ms->live);
+    k_ms_A<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, ctx->ms);
     if (fused_iter()) {
         k_ms_B3<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
                                                  ctx->ms, ctx->partials, ctx->gpart, ctx->counter);
@@ -622,7 +626,7 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
         }, s);
         if (st) return st;
         if ((st = read_ms_state(ctx, s))) return st;
-        if (!hs->live) break;
+        if (!hs->live || hs->stop_next) break;
         if (++guard > maxit / chunk + 4) break;  // cannot happen: the device caps iterations
     }
     if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in multi-shift CG");
