@@ -152,6 +152,56 @@ def thermalise(stag, L, rat, seed, ntraj=THERM):
     return info["plaq"] if info else None
 
 
+BATCH_LATTICES = [(16, 16, 16, 16), (24, 24, 24, 8), (32, 32, 32, 8)]
+BATCH_RHS = 96  # 8 pseudofermions x 12 shifts per lattice
+
+
+def batched_hop(stag, torch, nrep=10):
+    """The multi-lattice batched hop: 96 right-hand sides on each of 16^4,
+    24^3x8 and 32^3x8 (links exp(i 0.2 H)) in one launch, against one launch
+    per lattice and one launch per right-hand side.  Algorithmic bytes: links
+    384 B per output site once per lattice, 216 B per right-hand side and
+    output site (8 neighbours + output, FP32)."""
+    from paper_1106_5673_gb300 import synth
+    lats, ins = [], []
+    for i, dims in enumerate(BATCH_LATTICES):
+        L = stag.Lattice(dims)
+        L.load_gauge(synth.near_unit_links(dims, 0.2, 20 + i))
+        g = torch.Generator(device="cuda").manual_seed(30 + i)
+        x = torch.randn((BATCH_RHS, L.Vh, 3), dtype=torch.complex64, device="cuda", generator=g)
+        lats.append(L)
+        ins.append(x)
+    outs, cfg = stag.dslash_batch(lats, ins, out_par=1)  # tunes
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(nrep):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) * 1e-3 / nrep
+
+    t_batch = timed(lambda: stag.dslash_batch(lats, ins, outs, out_par=1))
+    for L, x, y in zip(lats, ins, outs):  # tune the per-lattice launches first
+        stag.dslash_batch([L], [x], [y], out_par=1)
+    t_per_lat = timed(lambda: [stag.dslash_batch([L], [x], [y], out_par=1)
+                               for L, x, y in zip(lats, ins, outs)])
+    t_per_rhs = timed(lambda: [L.apply_doe(x[j], y[j], stag.PREC_F32)
+                               for L, x, y in zip(lats, ins, outs) for j in range(BATCH_RHS)])
+    alg = sum(L.Vh * (384.0 + 216.0 * BATCH_RHS) for L in lats)
+    for L in lats:
+        L.close()
+    return {"lattices": [list(d) for d in BATCH_LATTICES], "rhs_per_lattice": BATCH_RHS,
+            "tuned": {"threads_per_block": cfg[0], "rhs_per_thread": cfg[1]},
+            "seconds_one_launch": t_batch, "seconds_launch_per_lattice": t_per_lat,
+            "seconds_launch_per_rhs": t_per_rhs, "algorithmic_bytes": alg,
+            "gbs_one_launch": alg / t_batch / 1e9}
+
+
 def kernel_table(stag, torch, L, params, path, top=14):
     """Per-kernel device time of one trajectory from CUPTI (torch.profiler):
     launches, total, share and average per kernel name; written to `path` and
@@ -383,7 +433,7 @@ def main():
             L2.close()
         compare["speedup_vs_f64"] = compare["f64"]["s_per_traj"] / value if world == 1 else None
 
-    t_e2e, roof, roof_large = None, None, None
+    t_e2e, roof, roof_large, batch = None, None, None, None
     link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
     if not args.no_extras:
         # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
@@ -397,6 +447,7 @@ def main():
         t_e2e = time.perf_counter() - t0
         roof = hop_roofline(stag, torch, DIMS)
         roof_large = hop_roofline(stag, torch, ROOF_DIMS)
+        batch = batched_hop(stag, torch)
     peak, peak_kind = _peaks()
     ktable = None
     if args.kernel_table:
@@ -445,6 +496,7 @@ def main():
         "cg_iters_per_traj": iters_timed,
         "compare_same_start": compare,
         "kernel_table": ktable,
+        "batched_hop": batch,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = compare["f64"]["cg_iters"] if compare else (REF_ITERS_PER_TRAJ or args.ref_iters)

@@ -87,6 +87,7 @@ enum { STAG_INT_LEAPFROG = 0, STAG_INT_OMELYAN = 1 };
 #define STAG_MAXSHIFT 32
 #define STAG_MAXPF 8
 #define STAG_MAXRHS 8 /* systems of one batched multi-shift solve */
+#define STAG_MAXLAT 8 /* lattices of one batched hop launch */
 
 typedef struct stag_ctx stag_ctx;
 
@@ -215,6 +216,22 @@ int stag_apply_M(stag_ctx *ctx, double mass, const void *in_even, void *out_even
  * string, since there is no context.  Asynchronous on `stream`. */
 int stag_apply_M_noalloc(const int dims[4], const double *links, double mass, const double *in_even,
                          double *out_even, void *stream);
+
+/* Batched hop: for each lattice l < nlat (each its own context, all on one
+ * device, any sizes), out[l][j] = D_{out_par, 1-out_par} in[l][j] for the
+ * nrhs[l] right-hand sides j, all in ONE persistent kernel launch whose
+ * blocks walk a list of (lattice, site block, group of right-hand sides)
+ * tiles, each link loaded once per tile and applied to the group (Eq. (4)).
+ * in[l], out[l]: FP32 complex device vectors [nrhs[l]][V_l/2][3], contiguous
+ * (canonical site order of the source and target parity).  prec:
+ * STAG_PREC_F32 or STAG_PREC_BF16 links.  The first call for a combination of
+ * lattice shapes, nrhs and prec tunes the block size and right-hand sides per
+ * thread by timing (synchronises; skipped, with defaults, while `stream` is
+ * being captured) and caches the choice; tuned_cfg (nullable) receives
+ * {threads per block, right-hand sides per thread}.  Otherwise asynchronous;
+ * capturable in a CUDA graph.  nlat <= STAG_MAXLAT. */
+int stag_dslash_batch(int nlat, stag_ctx *const *ctxs, const void *const *in, void *const *out,
+                      const int *nrhs, int out_par, int prec, int *tuned_cfg, void *stream);
 
 /* ---------------- solvers (Sec. 4.3, Eq. (13)) ---------------- */
 

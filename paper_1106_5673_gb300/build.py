@@ -14,7 +14,8 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_lib", "obj")
 LIB = os.path.join(HERE, "_lib", "libstag.so")
 SOURCES = ["capi.cu", "gauge.cu", "dslash.cu", "blas.cu", "solver.cu", "refine.cu", "msmulti.cu", "force.cu",
-           "rhmc.cu", "gcnn.cu", "noalloc.cu", "remez.cpp"]
+           "rhmc.cu", "gcnn.cu", "batch.cu", "noalloc.cu",
+           "remez.cpp"]
 HEADERS = ["lattice.cuh", "hop.cuh", "ms_common.cuh", "stag_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

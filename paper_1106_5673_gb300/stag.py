@@ -24,6 +24,7 @@ SOLVE_F64, SOLVE_MIXED, SOLVE_MIXED_BF16, SOLVE_F64FF, SOLVE_LEARNED = 0, 1, 2, 
 INT_LEAPFROG, INT_OMELYAN = 0, 1
 MAXSHIFT = 32
 MAXPF = 8
+MAXLAT = 8
 OMELYAN_LAMBDA = 0.1931833275037836
 
 
@@ -122,6 +123,8 @@ _SIGS = {
     "stag_net_create": (C.c_int, [_vp, C.c_uint, C.POINTER(_vp)]),
     "stag_net_destroy": (C.c_int, [_vp]),
     "stag_ctx_set_net": (C.c_int, [_vp, _vp]),
+    "stag_dslash_batch": (C.c_int, [C.c_int, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
+                                    C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int), _vp]),
     "stag_net_nweights": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int)]),
     "stag_net_get_weights": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_float)]),
     "stag_net_set_weights": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_float)]),
@@ -462,3 +465,25 @@ def fcg_solve(lattice, net, mass, shift, src, tol=1e-10, maxit=100000):
                               _ptr(src), _ptr(sol), tol, maxit, C.byref(info), _stream())
     lattice._chk(st)
     return sol, info
+
+
+def dslash_batch(lattices, ins, outs=None, out_par=1, prec=PREC_F32):
+    """One launch: outs[l][j] = D (to parity out_par) ins[l][j] for every
+    lattice l and right-hand side j; ins[l] complex64 CUDA tensors
+    [nrhs, V/2, 3].  Returns (outs, (threads per block, rhs per thread))."""
+    n = len(lattices)
+    if outs is None:
+        outs = [_torch().empty_like(x) for x in ins]
+    for L, x, y in zip(lattices, ins, outs):
+        if x.dim() != 3 or x.shape[1:] != (L.Vh, 3) or y.shape != x.shape or not x.is_contiguous() \
+                or not y.is_contiguous():
+            raise ValueError("bad batch vector shape")
+    hs = (_vp * n)(*[L._h for L in lattices])
+    a = (_vp * n)(*[x.data_ptr() for x in ins])
+    b = (_vp * n)(*[y.data_ptr() for y in outs])
+    nr = (C.c_int * n)(*[int(x.shape[0]) for x in ins])
+    cfg = (C.c_int * 2)()
+    st = lib().stag_dslash_batch(n, hs, a, b, nr, out_par, prec, cfg, _stream())
+    if st != OK:
+        raise StagError(st, lib().stag_last_error(lattices[0]._h).decode())
+    return outs, (cfg[0], cfg[1])
