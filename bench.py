@@ -202,6 +202,64 @@ def batched_hop(stag, torch, nrep=10):
             "gbs_one_launch": alg / t_batch / 1e9}
 
 
+def learned_preconditioner(stag, torch, L, shift, npairs=16, epochs=60):
+    """The gauge-covariant network preconditioner on the workload's own
+    lattice and lightest pole.  Two kinds of (source, solution) pairs:
+    'solved' (random b, x from the solver) and 'operator' (random x,
+    b = (M_ee + shift) x, exact, no solve); the network is trained on each,
+    then flexible CG with it is compared with plain CG (both FP64-accurate,
+    tol 1e-10) on a fresh source."""
+    from paper_1106_5673_gb300 import synth
+    dims = L.dims
+    b = torch.from_numpy(synth.gaussian_vector(dims, 999)).cuda()
+    out = {"lattice": list(dims), "shift": shift, "pairs": npairs, "epochs": epochs}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info = stag.fcg_solve(L, None, MASS, shift, b, tol=1e-10)
+    torch.cuda.synchronize()
+    out["plain_cg"] = {"iters": info.iters, "seconds": time.perf_counter() - t0,
+                       "true_resid": info.true_resid[0]}
+    for kind in ("solved", "operator"):
+        bs, xs = [], []
+        t0 = time.perf_counter()
+        for j in range(npairs):
+            v = torch.from_numpy(synth.gaussian_vector(dims, 500 + j)).cuda()
+            if kind == "solved":
+                sols, _ = L.multishift_solve(MASS, [shift], v, tol=1e-8, mode=stag.SOLVE_MIXED)
+                bs.append(v)
+                xs.append(sols[0])
+            else:
+                w = L.vector()
+                L.apply_M(MASS, v, w, stag.PREC_F64FF)
+                bs.append(w + shift * v)
+                xs.append(v)
+        torch.cuda.synchronize()
+        t_pairs = time.perf_counter() - t0
+        net = stag.Net(L, seed=5)
+        loss0 = net.loss_grad(bs, xs)
+        t0 = time.perf_counter()
+        loss = net.train(bs, xs, epochs=epochs, batch=4, lr=5e-3)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = stag.fcg_solve(L, net, MASS, shift, b, tol=1e-10)
+        torch.cuda.synchronize()
+        out[kind] = {"seconds_pairs": t_pairs, "seconds_train": t_train, "loss_before": loss0,
+                     "loss_after": loss, "fcg_iters": info.iters,
+                     "fcg_seconds": time.perf_counter() - t0, "true_resid": info.true_resid[0]}
+        net.close()
+    return out
+
+
+def _extra(fn, *a):
+    """An optional measurement: its failure is recorded in the line, not fatal."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        return {"error": "%s: %s" % (type(e).__name__, e)}
+
+
 def kernel_table(stag, torch, L, params, path, top=14):
     """Per-kernel device time of one trajectory from CUPTI (torch.profiler):
     launches, total, share and average per kernel name; written to `path` and
@@ -433,7 +491,7 @@ def main():
             L2.close()
         compare["speedup_vs_f64"] = compare["f64"]["s_per_traj"] / value if world == 1 else None
 
-    t_e2e, roof, roof_large, batch = None, None, None, None
+    t_e2e, roof, roof_large, batch, learned = None, None, None, None, None
     link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
     if not args.no_extras:
         # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
@@ -447,7 +505,8 @@ def main():
         t_e2e = time.perf_counter() - t0
         roof = hop_roofline(stag, torch, DIMS)
         roof_large = hop_roofline(stag, torch, ROOF_DIMS)
-        batch = batched_hop(stag, torch)
+        batch = _extra(batched_hop, stag, torch)
+        learned = _extra(learned_preconditioner, stag, torch, L, min(rat_act[2]))
     peak, peak_kind = _peaks()
     ktable = None
     if args.kernel_table:
@@ -497,6 +556,7 @@ def main():
         "compare_same_start": compare,
         "kernel_table": ktable,
         "batched_hop": batch,
+        "learned_preconditioner": learned,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = compare["f64"]["cg_iters"] if compare else (REF_ITERS_PER_TRAJ or args.ref_iters)

@@ -512,8 +512,10 @@ __global__ void k_axpby(long n, double a, const double2* __restrict__ x, double 
 // plain CG when net is null):
 //   alpha = <r,z>/<p,Ap>, x += alpha p, r -= alpha Ap, z' = K r,
 //   beta = <z', r - r_old>/<z, r_old>, p = z' + beta p.
-// FP64 vectors, FP64-accurate float-float operator; stops on the recursive
-// residual and reports the FP64-accurate true residual.
+// FP64 vectors, FP64-accurate float-float operator.  The recursion stops on
+// its own residual; the true residual b - A x is then computed and, if it is
+// still above tol, replaces the recursive one and the recursion restarts from
+// x with a target half as large (residual replacement; at most 8 restarts).
 int fcg_solve(stag_ctx* ctx, stag_net* net, double mass, double shift, const double2* b, double2* x, double tol,
               int maxit, int* iters, double* true_resid, cudaStream_t s) {
     const long n3 = 3L * ctx->g.Vh;
@@ -540,41 +542,49 @@ int fcg_solve(stag_ctx* ctx, stag_net* net, double mass, double shift, const dou
     int st;
     STAG_CUDA(ctx, cudaMemsetAsync(x, 0, vb, s));
     STAG_CUDA(ctx, cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, s));
-    if ((st = apply_K(r, z))) return st;
-    STAG_CUDA(ctx, cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, s));
-    if ((st = dot(b, b, 0)) || (st = dot(r, z, 1)) || (st = fetch(2))) return st;
+    if ((st = dot(b, b, 0)) || (st = fetch(1))) return st;
     const double bb = hd[0];
-    double rz = hd[1];
     int k = 0;
-    double rr = bb;
-    while (k < maxit && rr > tol * tol * bb) {
-        if ((st = mee_apply(ctx, STAG_PREC_F64FF, c, p, w, t, s))) return st;
-        if ((st = dot(p, w, 2)) || (st = fetch(3))) return st;
-        const double alpha = rz / hd[2];
-        STAG_CUDA(ctx, cudaMemcpyAsync(rold, r, vb, cudaMemcpyDeviceToDevice, s));
-        k_axpby<<<nb, 256, 0, s>>>(n3, alpha, p, 1.0, x);
-        k_axpby<<<nb, 256, 0, s>>>(n3, -alpha, w, 1.0, r);
-        ctx->nlaunch += 2;
-        if ((st = apply_K(r, zz))) return st;
-        // beta = <z', r - r_old> / <z, r_old>, computed as (<z',r> - <z',r_old>) / rz
-        if ((st = dot(r, r, 3)) || (st = dot(zz, r, 4)) || (st = dot(zz, rold, 5)) || (st = fetch(6))) return st;
-        rr = hd[3];
-        const double beta = (hd[4] - hd[5]) / rz;
-        rz = hd[4];
-        k_axpby<<<nb, 256, 0, s>>>(n3, 1.0, zz, beta, p);
+    double target = tol, rr_true = bb;
+    for (int restart = 0; restart <= 8 && bb > 0.0; restart++) {
+        if ((st = apply_K(r, z))) return st;
+        STAG_CUDA(ctx, cudaMemcpyAsync(p, z, vb, cudaMemcpyDeviceToDevice, s));
+        if ((st = dot(r, z, 1)) || (st = dot(r, r, 3)) || (st = fetch(4))) return st;
+        double rz = hd[1], rr = hd[3];
+        while (k < maxit && rr > target * target * bb) {
+            if ((st = mee_apply(ctx, STAG_PREC_F64FF, c, p, w, t, s))) return st;
+            if ((st = dot(p, w, 2)) || (st = fetch(3))) return st;
+            const double alpha = rz / hd[2];
+            STAG_CUDA(ctx, cudaMemcpyAsync(rold, r, vb, cudaMemcpyDeviceToDevice, s));
+            k_axpby<<<nb, 256, 0, s>>>(n3, alpha, p, 1.0, x);
+            k_axpby<<<nb, 256, 0, s>>>(n3, -alpha, w, 1.0, r);
+            ctx->nlaunch += 2;
+            if ((st = apply_K(r, zz))) return st;
+            // beta = <z', r - r_old> / <z, r_old>, computed as (<z',r> - <z',r_old>) / rz
+            if ((st = dot(r, r, 3)) || (st = dot(zz, r, 4)) || (st = dot(zz, rold, 5)) || (st = fetch(6))) return st;
+            rr = hd[3];
+            const double beta = (hd[4] - hd[5]) / rz;
+            rz = hd[4];
+            k_axpby<<<nb, 256, 0, s>>>(n3, 1.0, zz, beta, p);
+            ctx->nlaunch++;
+            std::swap(z, zz);
+            k++;
+            if (!isfinite(rr) || !isfinite(beta))
+                return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in FCG");
+        }
+        STAG_LAUNCH_CHECK(ctx, "fcg");
+        // FP64-accurate true residual; it replaces the recursive one
+        if ((st = mee_apply(ctx, STAG_PREC_F64FF, c, x, w, t, s))) return st;
+        k_axpby<<<nb, 256, 0, s>>>(n3, 1.0, b, -1.0, w);
         ctx->nlaunch++;
-        std::swap(z, zz);
-        k++;
-        if (!isfinite(rr) || !isfinite(beta)) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in FCG");
+        if ((st = dot(w, w, 6)) || (st = fetch(7))) return st;
+        rr_true = hd[6];
+        if (rr_true <= tol * tol * bb || k >= maxit) break;
+        STAG_CUDA(ctx, cudaMemcpyAsync(r, w, vb, cudaMemcpyDeviceToDevice, s));
+        target *= 0.5;
     }
-    STAG_LAUNCH_CHECK(ctx, "fcg");
-    // FP64-accurate true residual
-    if ((st = mee_apply(ctx, STAG_PREC_F64FF, c, x, w, t, s))) return st;
-    k_axpby<<<nb, 256, 0, s>>>(n3, 1.0, b, -1.0, w);
-    ctx->nlaunch++;
-    if ((st = dot(w, w, 6)) || (st = fetch(7))) return st;
     *iters = k;
-    *true_resid = sqrt(hd[6] / bb);
+    *true_resid = (bb > 0.0) ? sqrt(rr_true / bb) : 0.0;
     return (*true_resid <= tol * 1.00000005) ? STAG_OK : stag_fail(ctx, STAG_ERR_NOCONV, "FCG did not converge");
 }
 

@@ -581,13 +581,32 @@ int true_residual2(stag_ctx* ctx, int prec, double c, const double2* b, const do
 
 // Shifted CG with vectors of type R and links LP.  b: FP64 source.  On
 // return the FP64 solutions are in xout (n contiguous vectors).
+// Runs 16-iteration chunks of the shifted CG until the device state stops.
 template <typename R, int LP>
-int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* b, double2* xout,
-            double tol, int maxit, stag_solve_info* info, cudaStream_t s) {
+static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s) {
+    MSState* hs = ctx->ms_host;
+    const int chunk = env_int("STAG_CHUNK", 16);
+    char key[64];
+    snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), hop_tpb(ctx, LP),
+             bf.xk);
+    int guard = 0, st;
+    for (;;) {
+        st = run_chunk(ctx, key, (fused_iter() ? 3 : 4) * chunk, [&](cudaStream_t cs) {
+            for (int i = 0; i < chunk; i++) launch_ms_iter<R, LP>(ctx, U, bf, cs);
+        }, s);
+        if (st) return st;
+        if ((st = read_ms_state(ctx, s))) return st;
+        if (!hs->live || hs->stop_next) break;
+        if (++guard > maxit / chunk + 4) break;  // cannot happen: the device caps iterations
+    }
+    if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in multi-shift CG");
+    return STAG_OK;
+}
+
+template <typename R, int LP>
+static MSBufs ms_bufs(stag_ctx* ctx, double2* xout) {
     typedef typename VT<R>::T V2;
-    const Geom& g = ctx->g;
-    const long n3 = 3L * g.Vh;
-    const size_t vb = sizeof(V2) * n3;
+    const size_t vb = sizeof(V2) * 3L * ctx->g.Vh;
     const bool f64 = (sizeof(R) == 8);
     MSBufs bf;
     bf.r = ws_get(ctx, f64 ? WS_R64 : WS_R32, vb);
@@ -596,8 +615,45 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
     bf.t = ws_get(ctx, f64 ? WS_T64 : WS_T32, vb);
     bf.pk = ws_get(ctx, f64 ? WS_PK64 : WS_PK32, vb * STAG_MAXSHIFT);
     bf.xk = ws_get(ctx, f64 ? WS_XK64 : WS_XK32, vb * STAG_MAXSHIFT);
+    if (f64) bf.xk = xout;
+    return bf;
+}
+
+// FP64 modes: the recursion stops shift k when its recursive residual meets
+// tol; if its true residual (checked afterwards) is still above tol, the
+// same Krylov recursion is resumed for those shifts alone with a tolerance
+// ten times tighter (the state, r, p, p_k and x_k are still on the device).
+template <typename R, int LP>
+static int ms_continue(stag_ctx* ctx, double2* xout, const int* ks, int nk, int maxit, stag_solve_info* info,
+                       cudaStream_t s) {
+    MSState* hs = ctx->ms_host;  // the state read after the last chunk
+    MSBufs bf = ms_bufs<R, LP>(ctx, xout);
+    const int it0 = hs->iter;
+    int before[STAG_MAXSHIFT];
+    for (int k = 0; k < hs->n; k++) before[k] = hs->iters_shift[k];
+    hs->tol2bb *= 0.01;
+    for (int i = 0; i < nk; i++) hs->active[ks[i]] = 1;
+    hs->n_active = nk;
+    hs->live = 1;
+    hs->stop_next = 0;
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->ms, hs, sizeof(MSState), cudaMemcpyHostToDevice, s));
+    const int st = ms_run<R, LP>(ctx, make_links(ctx, LP), bf, maxit, s);
+    if (st) return st;
+    info->iters += hs->iter - it0;
+    info->matvecs += hs->iter - it0;
+    for (int k = 0; k < hs->n; k++) info->iters_shift[k] += hs->iters_shift[k] - before[k];
+    return STAG_OK;
+}
+
+template <typename R, int LP>
+int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* b, double2* xout,
+            double tol, int maxit, stag_solve_info* info, cudaStream_t s) {
+    typedef typename VT<R>::T V2;
+    const Geom& g = ctx->g;
+    const long n3 = 3L * g.Vh;
+    const bool f64 = (sizeof(R) == 8);
+    MSBufs bf = ms_bufs<R, LP>(ctx, xout);  // FP64: x_k accumulate straight into the output
     if (!bf.r || !bf.p || !bf.w || !bf.t || !bf.pk || !bf.xk) return stag_fail(ctx, STAG_ERR_OOM, "solver workspace");
-    if (f64) bf.xk = xout;  // FP64: accumulate straight into the output
     Links U = make_links(ctx, LP);
 
     // scalar state
@@ -615,21 +671,7 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
     ctx->nlaunch++;
     STAG_LAUNCH_CHECK(ctx, "ms init");
 
-    const int chunk = env_int("STAG_CHUNK", 16);
-    char key[64];
-    snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), hop_tpb(ctx, LP),
-             bf.xk);
-    int guard = 0;
-    for (;;) {
-        st = run_chunk(ctx, key, (fused_iter() ? 3 : 4) * chunk, [&](cudaStream_t cs) {
-            for (int i = 0; i < chunk; i++) launch_ms_iter<R, LP>(ctx, U, bf, cs);
-        }, s);
-        if (st) return st;
-        if ((st = read_ms_state(ctx, s))) return st;
-        if (!hs->live || hs->stop_next) break;
-        if (++guard > maxit / chunk + 4) break;  // cannot happen: the device caps iterations
-    }
-    if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in multi-shift CG");
+    if ((st = ms_run<R, LP>(ctx, U, bf, maxit, s))) return st;
     if (info) {
         info->iters += hs->iter;
         info->matvecs += hs->iter;
@@ -920,6 +962,55 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
     const double bb = ctx->hscal[1];
     double rr[STAG_MAXSHIFT];
     for (int k = 0; k < n; k++) rr[k] = ctx->hscal[100 + k];
+    for (int round = 0; round < 3 && (mode == STAG_SOLVE_F64 || mode == STAG_SOLVE_F64FF) && bb > 0.0; round++) {
+        // shifts still updated by the last iteration can resume the recursion;
+        // a shift frozen earlier cannot (its p_k and zeta_k are stale) and is
+        // refined by the batched CG instead
+        int ks[STAG_MAXSHIFT], nk = 0, kr[STAG_MAXSHIFT], nr = 0;
+        for (int k = 0; k < n; k++)
+            if (rr[k] > tol * tol * bb) {
+                if (ctx->ms_host->iters_shift[k] == ctx->ms_host->iter)
+                    ks[nk++] = k;
+                else
+                    kr[nr++] = k;
+            }
+        if (nr > 0) {
+            float2* R = (float2*)ws_get(ctx, WS_BR, sizeof(float2) * n3 * STAG_MAXSHIFT);
+            if (!R) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
+            RefSlots S;
+            for (int k = 0; k < n; k++) {
+                S.b[k] = src;
+                S.x[k] = X + k * n3;
+                S.c[k] = mass * mass + shifts[k];
+                S.bb[k] = bb;
+            }
+            double rr2[STAG_MAXSHIFT];
+            if ((st = batched_true_residuals(ctx, S, kr, nr, R, rr2, s))) return st;
+            int its[STAG_MAXSHIFT] = {0}, rel = 0, mv = 0;
+            if ((st = refine_batched(ctx, LP32, S, kr, nr, R, tol, maxit, rr2, its, &rel, &mv, s))) return st;
+            for (int i = 0; i < nr; i++) {
+                rr[kr[i]] = rr2[kr[i]];
+                info->refine_iters[kr[i]] += its[kr[i]];
+            }
+            info->reliable_updates += rel;
+            info->matvecs += mv + nr;
+        }
+        if (nk == 0) break;
+        st = (mode == STAG_SOLVE_F64) ? ms_continue<double, LP64>(ctx, X, ks, nk, maxit, info, s)
+                                      : ms_continue<double, LPFF>(ctx, X, ks, nk, maxit, info, s);
+        if (st) return st;
+        for (int i = 0; i < nk; i++) {
+            const int k = ks[i];
+            if ((st = true_residual2(ctx, check_prec, mass * mass + shifts[k], src, X + k * n3, w64, t64, nullptr,
+                                     nullptr, ctx->dscal + 100 + k, s)))
+                return st;
+        }
+        STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal + 100, ctx->dscal + 100, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                                       s));
+        STAG_CUDA(ctx, cudaStreamSynchronize(s));
+        info->matvecs += nk;
+        for (int i = 0; i < nk; i++) rr[ks[i]] = ctx->hscal[100 + ks[i]];
+    }
     int status = STAG_OK;
     for (int k = 0; k < n; k++) {
         if (bb == 0.0) {
