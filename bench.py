@@ -202,6 +202,56 @@ def batched_hop(stag, torch, nrep=10):
             "gbs_one_launch": alg / t_batch / 1e9}
 
 
+def batched_solve(stag, torch):
+    """The batched workload as solves: 8 pseudofermion sources x 12 shifts
+    (poles of the degree-12 x^{-1/2} approximation on [1e-4, 64]) at m 0.01
+    on each of 16^4, 24^3x8 and 32^3x8 (links exp(i 0.2 H)), mixed mode to
+    1e-10.  Each lattice's 8 systems advance together in one multi-system
+    shifted CG (multi-RHS hops); the three lattices run one after another,
+    then concurrently on three streams (host threads; the library releases
+    the interpreter while it works)."""
+    import threading
+    from paper_1106_5673_gb300 import synth
+    m = 0.01
+    _, _, shifts, _ = stag.remez(-0.5, m * m, 64.0, 12)
+    lats, srcs = [], []
+    for i, dims in enumerate(BATCH_LATTICES):
+        L = stag.Lattice(dims)
+        L.load_gauge(synth.near_unit_links(dims, 0.2, 40 + i))
+        lats.append(L)
+        srcs.append([torch.from_numpy(synth.gaussian_vector(dims, 60 + 10 * i + j)).cuda() for j in range(8)])
+    for L, b in zip(lats, srcs):  # warm-up: tuning and graph capture
+        L.multishift_solve_multi(m, shifts, b, tol=1e-10, mode=stag.SOLVE_MIXED)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = [L.multishift_solve_multi(m, shifts, b, tol=1e-10, mode=stag.SOLVE_MIXED) for L, b in zip(lats, srcs)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    out = [None] * len(lats)
+    streams = [torch.cuda.Stream() for _ in lats]
+    torch.cuda.synchronize()
+
+    def work(i):
+        with torch.cuda.stream(streams[i]):
+            out[i] = lats[i].multishift_solve_multi(m, shifts, srcs[i], tol=1e-10, mode=stag.SOLVE_MIXED)
+            streams[i].synchronize()
+
+    th = [threading.Thread(target=work, args=(i,)) for i in range(len(lats))]
+    t0 = time.perf_counter()
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    t_con = time.perf_counter() - t0
+    maxres = max(inf.true_resid[k] for _, infos in out for inf in infos for k in range(len(shifts)))
+    iters = [[inf.iters for inf in infos] for _, infos in res]
+    for L in lats:
+        L.close()
+    return {"lattices": [list(d) for d in BATCH_LATTICES], "systems_per_lattice": 8, "shifts": len(shifts),
+            "mass": m, "tol": 1e-10, "seconds_sequential": t_seq, "seconds_concurrent": t_con,
+            "multishift_iters": iters, "max_true_resid": maxres}
+
+
 def learned_preconditioner(stag, torch, L, shift, npairs=16, epochs=60):
     """The gauge-covariant network preconditioner on the workload's own
     lattice and lightest pole.  Two kinds of (source, solution) pairs:
@@ -491,7 +541,7 @@ def main():
             L2.close()
         compare["speedup_vs_f64"] = compare["f64"]["s_per_traj"] / value if world == 1 else None
 
-    t_e2e, roof, roof_large, batch, learned = None, None, None, None, None
+    t_e2e, roof, roof_large, batch, bsolve, learned = None, None, None, None, None, None
     link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
     if not args.no_extras:
         # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
@@ -506,6 +556,7 @@ def main():
         roof = hop_roofline(stag, torch, DIMS)
         roof_large = hop_roofline(stag, torch, ROOF_DIMS)
         batch = _extra(batched_hop, stag, torch)
+        bsolve = _extra(batched_solve, stag, torch)
         learned = _extra(learned_preconditioner, stag, torch, L, min(rat_act[2]))
     peak, peak_kind = _peaks()
     ktable = None
@@ -556,6 +607,7 @@ def main():
         "compare_same_start": compare,
         "kernel_table": ktable,
         "batched_hop": batch,
+        "batched_solve": bsolve,
         "learned_preconditioner": learned,
     }
     if rank == 0 and world == 1 and not args.no_cpu:

@@ -501,10 +501,14 @@ int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int 
     STAG_CUDA(ctx, cudaMemcpyAsync(ctx->bcg, hs, sizeof(BCGState), cudaMemcpyHostToDevice, s));
 
     char key[64];
-    snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d", lp, nk, it.chunk, it.fused, it.tpb);
     int remaining = nk;
     int done[STAG_MAXSHIFT] = {0};
     while (remaining > 0) {
+        // the grids cover the right-hand sides active at the start of the chunk
+        // (the device only removes slots within a chunk); one graph per size
+        it.ny_hop = (hs->n_act + NR - 1) / NR;
+        it.ny_blas = hs->n_act;
+        snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d", lp, hs->n_act, it.chunk, it.fused, it.tpb);
         int st = run_graph_chunk(ctx, key, (it.fused ? 3 : 4) * it.chunk, enqueue_b, &it, s);
         if (st) return st;
         STAG_CUDA(ctx, cudaMemcpyAsync(hs, ctx->bcg, sizeof(BCGState), cudaMemcpyDeviceToHost, s));
