@@ -50,6 +50,42 @@ def _metric():
     return "s/trajectory (RHMC 32^3x8, 1e-10 residual)"
 
 
+def replica_seeds(rank):
+    """Replicas (one independent chain per rank, no data-path collective):
+    every seed depends on the rank."""
+    return {"links": 1 + rank, "therm": 50 + rank, "rng": 100 + rank}
+
+
+def max_over_ranks(t, world):
+    """The slowest rank's time (all ranks receive it)."""
+    if world <= 1:
+        return t
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_value(t_max, steps, world):
+    """Whole-job seconds per trajectory: N ranks each ran `steps` trajectories
+    in t_max seconds."""
+    return t_max / (steps * world)
+
+
+def workload_config(therm=THERM, world=1):
+    """The workload as both arms report it (config)."""
+    return {"workload": WORKLOAD, "lattice": list(DIMS), "beta": BETA, "mass": MASS,
+            "integrator": "omelyan", "nsteps": NSTEPS, "tau": TAU, "rational_degree": DEG,
+            "rational_range": [LO, HI], "tol": TOL,
+            "parallelism": "replicas" if world > 1 else "single",
+            "start": {"links": "exp(i 0.3 H)",
+                      "thermalisation": "%d pure-gauge MD trajectories (tau 1, %d Omelyan steps, "
+                                        "no Metropolis)" % (therm, THERM_STEPS)},
+            "l2": "working set > L2 (links fp64+fp32+bf16 ~176 MB, solver vectors ~200 MB)"}
+
+
 def _params(stag, rat_hb, rat_act, mode, traj, seed):
     return stag.make_params(BETA, MASS, TAU, NSTEPS, stag.INT_OMELYAN, rat_hb, rat_act, rat_act,
                             tol_md=TOL, tol_metro=TOL, mode_md=mode, mode_metro=mode, seed=seed,
@@ -408,7 +444,7 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "lattice": list(DIMS)},
+            "config": workload_config(),
             "cpu_baseline": {"value": v, "unit": "s/trajectory", "cores": 1, "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": "s/trajectory", "h2d_bytes_per_step": 0,
@@ -482,8 +518,9 @@ def main():
     h0, ha, hb, err_hb = stag.remez(0.25, LO, HI, DEG)
     rat_act, rat_hb = (a0, a, b), (h0, ha, hb)
     L = stag.Lattice(DIMS)
-    L.load_gauge(synth.near_unit_links(DIMS, 0.3, 1 + rank))
-    plaq_start = thermalise(stag, L, rat_act, 50 + rank, args.therm)
+    seeds = replica_seeds(rank)
+    L.load_gauge(synth.near_unit_links(DIMS, 0.3, seeds["links"]))
+    plaq_start = thermalise(stag, L, rat_act, seeds["therm"], args.therm)
     U0 = L.store_gauge()
 
     MODES = {"mixed": stag.SOLVE_MIXED, "f64": stag.SOLVE_F64, "ff": stag.SOLVE_F64FF,
@@ -492,7 +529,7 @@ def main():
 
     # warm-up trajectories (untimed), then K timed ones
     for i in range(args.warmup):
-        L.md_trajectory(_params(stag, rat_hb, rat_act, mode, i, 100 + rank))
+        L.md_trajectory(_params(stag, rat_hb, rat_act, mode, i, seeds["rng"]))
     n0 = L.launch_count()
     clocks = ClockSampler(_gpu_uuid(torch, local))
     barrier()
@@ -505,20 +542,16 @@ def main():
         if args.profile_window and k == 0:
             torch.cuda.profiler.start()
         infos.append(L.md_trajectory(_params(stag, rat_hb, rat_act, mode, args.warmup + k,
-                                             100 + rank)))
+                                             seeds["rng"])))
         if args.profile_window and k == 0:
             torch.cuda.profiler.stop()
     e1.record()
     torch.cuda.synchronize()
     barrier()
     ck = clocks.stop()
-    t = e0.elapsed_time(e1) * 1e-3
-    if world > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(e0.elapsed_time(e1) * 1e-3, world)
     launches = L.launch_count() - n0
-    value = t / (args.steps * world)
+    value = whole_job_value(t, args.steps, world)
     iters_timed = sum(i["cg_iters"] for i in infos) / len(infos)
 
     # the plain FP64 GPU form and the float-float form of the next trajectory,
@@ -534,7 +567,7 @@ def main():
             L2.load_gauge(Ustart)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            i2 = L2.md_trajectory(_params(stag, rat_hb, rat_act, m, traj, 100 + rank))
+            i2 = L2.md_trajectory(_params(stag, rat_hb, rat_act, m, traj, seeds["rng"]))
             torch.cuda.synchronize()
             compare[name] = {"s_per_traj": time.perf_counter() - t0, "cg_iters": i2["cg_iters"],
                              "dH": i2["dH"], "accepted": i2["accepted"]}
@@ -549,7 +582,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         L.load_gauge(Uh)
-        L.md_trajectory(_params(stag, rat_hb, rat_act, mode, 999, 100 + rank))
+        L.md_trajectory(_params(stag, rat_hb, rat_act, mode, 999, seeds["rng"]))
         Uh = L.store_gauge()
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
@@ -561,7 +594,7 @@ def main():
     peak, peak_kind = _peaks()
     ktable = None
     if args.kernel_table:
-        ktable = kernel_table(stag, torch, L, _params(stag, rat_hb, rat_act, mode, 998, 100 + rank),
+        ktable = kernel_table(stag, torch, L, _params(stag, rat_hb, rat_act, mode, 998, seeds["rng"]),
                               args.kernel_table)
 
     line = {
@@ -569,16 +602,9 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "lattice": list(DIMS), "beta": BETA, "mass": MASS,
-                   "integrator": "omelyan", "nsteps": NSTEPS, "tau": TAU, "rational_degree": DEG,
-                   "rational_range": [LO, HI], "rational_err": [err_act, err_hb], "tol": TOL,
-                   "solver": "mixed: fp32 multishift + fp64 reliable-update refinement",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "start": {"links": "exp(i 0.3 H), seed %d" % (1 + rank),
-                             "thermalisation": "%d pure-gauge MD trajectories (tau 1, %d Omelyan "
-                                               "steps, no Metropolis)" % (args.therm, THERM_STEPS),
-                             "plaquette": plaq_start},
-                   "l2": "working set > L2 (links fp64+fp32+bf16 ~176 MB, solver vectors ~200 MB)"},
+        "config": dict(workload_config(args.therm, world),
+                       solver="mixed: fp32 multishift + fp64 reliable-update refinement",
+                       rational_err=[err_act, err_hb], start_plaquette=plaq_start),
         # the FP32 even/odd hop that the solver kernels (k_ms_A/B3, k_b_A/B3)
         # share, on the roofline lattice (working set > 4x L2); algorithmic
         # bytes 600 per output site, traffic from the ncu capture
