@@ -176,12 +176,12 @@ def hop_roofline(stag, torch, dims, nrep=30):
             "gflops": 570.0 * Vh / t / 1e9, "dims": list(dims)}
 
 
-def thermalise(stag, L, rat, seed, ntraj=THERM):
+def thermalise(stag, L, rat, seed, ntraj=THERM, beta=BETA):
     """Pure-gauge molecular dynamics (npf = 0, every trajectory kept) from the
     smooth start; returns the final plaquette."""
     info = None
     for i in range(ntraj):
-        p = stag.make_params(BETA, MASS, 1.0, THERM_STEPS, stag.INT_OMELYAN, rat, rat, rat, npf=0,
+        p = stag.make_params(beta, MASS, 1.0, THERM_STEPS, stag.INT_OMELYAN, rat, rat, rat, npf=0,
                              mode_md=stag.SOLVE_MIXED, mode_metro=stag.SOLVE_MIXED, seed=seed,
                              traj=i, no_metropolis=1)
         info = L.md_trajectory(p)
@@ -286,6 +286,45 @@ def batched_solve(stag, torch):
     return {"lattices": [list(d) for d in BATCH_LATTICES], "systems_per_lattice": 8, "shifts": len(shifts),
             "mass": m, "tol": 1e-10, "seconds_sequential": t_seq, "seconds_concurrent": t_con,
             "multishift_iters": iters, "max_true_resid": maxres}
+
+
+def reversibility(stag, torch, nmd=10, ngauge=2):
+    """The paper's reversibility test (Sec. 4.4) on its 4x16^3 lattice at
+    beta 5.264, am 0.01335, two pseudofermions, degree-8 MD and degree-15
+    Metropolis rationals, multi-step 2MN (n_md steps, ngauge gauge steps per
+    position update): integrate to tau = 1, flip the momenta, integrate back;
+    Delta C and Delta M per degree of freedom, FP64 and mixed mode.  Start:
+    60 pure-gauge MD trajectories from exp(i 0.3 H)."""
+    from paper_1106_5673_gb300 import synth
+    dims, beta, m = (16, 16, 16, 4), 5.264, 0.01335
+    lo, hi = m * m / 2, 64.0
+    a = stag.remez(-0.25, lo, hi, 8)[:3]      # x^{-1/(2 npf)}, npf = 2
+    am = stag.remez(-0.25, lo, hi, 15)[:3]
+    h = stag.remez(0.125, lo, hi, 15)[:3]     # x^{+1/(4 npf)}
+    L = stag.Lattice(dims)
+    L.load_gauge(synth.near_unit_links(dims, 0.3, 70))
+    thermalise(stag, L, a, 71, beta=beta)
+    U0 = L.store_gauge()
+    W0 = synth.gaussian_momenta(dims, 72)
+    phis = torch.stack([L.rational_apply(m, h, L.pf_gaussian(73, 0, pf), tol=1e-10)[0] for pf in range(2)])
+    dof = 4 * 8 * int(np.prod(dims))
+    out = {"lattice": list(dims), "beta": beta, "mass": m, "npf": 2, "md_degree": 8, "metro_degree": 15,
+           "n_md": nmd, "ngauge": ngauge, "plaquette": L.plaquette()}
+    for name, mode in (("f64", stag.SOLVE_F64), ("mixed", stag.SOLVE_MIXED)):
+        p = stag.make_params(beta, m, 1.0, nmd, stag.INT_OMELYAN, h, am, a, npf=2, tol_md=1e-10,
+                             tol_metro=1e-10, mode_md=mode, mode_metro=mode, ngauge=ngauge)
+        L.load_gauge(U0)
+        L.load_momenta(W0)
+        t0 = time.perf_counter()
+        it, _ = L.md_integrate(p, phis)
+        t_md = time.perf_counter() - t0
+        L.load_momenta(-L.store_momenta())
+        L.md_integrate(p, phis)
+        dC = float(np.sqrt((np.abs(L.store_gauge() - U0) ** 2).sum() / dof))
+        dM = float(np.sqrt(((L.store_momenta() + W0) ** 2).sum() / dof))
+        out[name] = {"delta_C": dC, "delta_M": dM, "cg_iters": it, "seconds_md": t_md}
+    L.close()
+    return out
 
 
 def learned_preconditioner(stag, torch, L, shift, npairs=16, epochs=60):
@@ -574,7 +613,7 @@ def main():
             L2.close()
         compare["speedup_vs_f64"] = compare["f64"]["s_per_traj"] / value if world == 1 else None
 
-    t_e2e, roof, roof_large, batch, bsolve, learned = None, None, None, None, None, None
+    t_e2e, roof, roof_large, batch, bsolve, learned, revers = None, None, None, None, None, None, None
     link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
     if not args.no_extras:
         # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
@@ -590,6 +629,7 @@ def main():
         roof_large = hop_roofline(stag, torch, ROOF_DIMS)
         batch = _extra(batched_hop, stag, torch)
         bsolve = _extra(batched_solve, stag, torch)
+        revers = _extra(reversibility, stag, torch)
         learned = _extra(learned_preconditioner, stag, torch, L, min(rat_act[2]))
     peak, peak_kind = _peaks()
     ktable = None
@@ -635,6 +675,7 @@ def main():
         "batched_hop": batch,
         "batched_solve": bsolve,
         "learned_preconditioner": learned,
+        "reversibility": revers,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = compare["f64"]["cg_iters"] if compare else (REF_ITERS_PER_TRAJ or args.ref_iters)

@@ -307,6 +307,18 @@ int stag_kinetic(stag_ctx *ctx, double *out, void *stream);
  * rejection the gauge field is restored.  Synchronises. */
 int stag_md_trajectory(stag_ctx *ctx, const stag_params *p, stag_traj_info *out, void *stream);
 
+/* Molecular dynamics alone (Sec. 2.1, point 3 of the Phi algorithm): integrates
+ * Hamilton's equations over p->tau with the context's current links and
+ * momenta (stag_load_gauge / stag_load_momenta) and the pseudofermions phi
+ * held fixed (p->npf FP64 device vectors, even sites, contiguous with stride
+ * V/2 x 3 complex), using p's integrator, force rational, MD tolerance and
+ * solver mode; no heatbath, no Metropolis test.  The reversibility test of
+ * Sec. 4.4 flips the momenta (store, negate, load) and integrates again.
+ * *cg_iters, *n_force (nullable) receive the solver iterations and fermion
+ * force evaluations.  Synchronises. */
+int stag_md_integrate(stag_ctx *ctx, const stag_params *p, const double *phi, long long *cg_iters, int *n_force,
+                      void *stream);
+
 /* ---------------- learned preconditioner (no counterpart in the paper) ------
  * A gauge-covariant network K = restrict_even L3 L2 L1 embed_even with
  * channels 1 -> 8 -> 8 -> 1; each layer is a parallel-transport convolution

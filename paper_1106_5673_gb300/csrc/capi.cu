@@ -6,6 +6,8 @@
 #include "stag_internal.h"
 
 int rhmc_trajectory(stag_ctx* ctx, const stag_params* p, stag_traj_info* out, cudaStream_t s);
+int md_integrate_public(stag_ctx* ctx, const stag_params* p, const double2* phi, long long* iters, int* nforce,
+                        cudaStream_t s);
 int gauge_force_internal_prec(stag_ctx* ctx, double beta, double* F, int accumulate, int prec32, cudaStream_t s);
 
 // ---------------------------------------------------------------- errors
@@ -442,10 +444,7 @@ int stag_kinetic(stag_ctx* ctx, double* out, void* stream) {
 
 // ---------------------------------------------------------------- trajectory
 
-int stag_md_trajectory(stag_ctx* ctx, const stag_params* p, stag_traj_info* out, void* stream) {
-    CHECK_CTX(ctx);
-    CHECK_GAUGE(ctx);
-    if (!p || !out) return stag_fail(ctx, STAG_ERR_ARG, "null params or output");
+static int check_params(stag_ctx* ctx, const stag_params* p) {
     if (p->nsteps < 1 || !(p->tau > 0) || p->npf < 0 || p->npf > STAG_MAXPF || p->maxit < 1 || p->ngauge < 0 ||
         p->ngauge > 1000)
         return stag_fail(ctx, STAG_ERR_ARG, "bad trajectory parameters");
@@ -454,7 +453,33 @@ int stag_md_trajectory(stag_ctx* ctx, const stag_params* p, stag_traj_info* out,
     const stag_rational* rs[3] = {&p->hb, &p->act, &p->force};
     for (auto r : rs)
         if (r->n < 1 || r->n > STAG_MAXSHIFT) return stag_fail(ctx, STAG_ERR_ARG, "bad rational degree");
+    return STAG_OK;
+}
+
+int stag_md_trajectory(stag_ctx* ctx, const stag_params* p, stag_traj_info* out, void* stream) {
+    CHECK_CTX(ctx);
+    CHECK_GAUGE(ctx);
+    if (!p || !out) return stag_fail(ctx, STAG_ERR_ARG, "null params or output");
+    int st = check_params(ctx, p);
+    if (st) return st;
     return rhmc_trajectory(ctx, p, out, S(stream));
+}
+
+int stag_md_integrate(stag_ctx* ctx, const stag_params* p, const double* phi, long long* cg_iters, int* n_force,
+                      void* stream) {
+    CHECK_CTX(ctx);
+    CHECK_GAUGE(ctx);
+    if (!p) return stag_fail(ctx, STAG_ERR_ARG, "null params");
+    int st = check_params(ctx, p);
+    if (st) return st;
+    if (p->npf > 0 && !phi) return stag_fail(ctx, STAG_ERR_ARG, "null pseudofermions");
+    long long it = 0;
+    int nf = 0;
+    if ((st = md_integrate_public(ctx, p, (const double2*)phi, &it, &nf, S(stream)))) return st;
+    STAG_CUDA(ctx, cudaStreamSynchronize(S(stream)));
+    if (cg_iters) *cg_iters = it;
+    if (n_force) *n_force = nf;
+    return STAG_OK;
 }
 
 }  // extern "C"

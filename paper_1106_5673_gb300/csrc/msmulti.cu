@@ -325,8 +325,10 @@ int multishift_solve_multi(stag_ctx* ctx, double mass, int nsys, int n, const do
                                     X + (size_t)r * STAG_MAXSHIFT * n3, (long)g.Vh * n, s)))
                 return st;
 
-    // FP64-accurate check of every (system, shift); mixed modes refine those
-    // above tolerance, up to 32 pairs per batch
+    // FP64-accurate check of every (system, shift); those above tolerance are
+    // refined by the batched CG, up to 32 pairs per batch (in the FP64 modes
+    // this only catches a recursion that stopped with its true residual just
+    // above tol)
     float2* Rres = (float2*)ws_get(ctx, WS_BR, sizeof(float2) * n3 * STAG_MAXSHIFT);
     if (!Rres) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
     int status = STAG_OK;
@@ -347,7 +349,7 @@ int multishift_solve_multi(stag_ctx* ctx, double mass, int nsys, int n, const do
         if ((st = batched_true_residuals(ctx, S, all, np, Rres, rr, s))) return st;
         int ks[STAG_MAXSHIFT], nk = 0;
         for (int j = 0; j < np; j++)
-            if (!f64 && S.bb[j] > 0.0 && rr[j] > tol * tol * S.bb[j]) ks[nk++] = j;
+            if (S.bb[j] > 0.0 && rr[j] > tol * tol * S.bb[j]) ks[nk++] = j;
         int its[STAG_MAXSHIFT] = {0}, rel = 0, mv = 0;
         if (nk > 0 && (st = refine_batched(ctx, LP32, S, ks, nk, Rres, tol, maxit, rr, its, &rel, &mv, s)))
             return st;

@@ -117,6 +117,8 @@ _SIGS = {
     "stag_pf_gaussian": (C.c_int, [_vp, C.c_uint32, C.c_uint32, C.c_int, _vp, _vp]),
     "stag_kinetic": (C.c_int, [_vp, _dp, _vp]),
     "stag_md_trajectory": (C.c_int, [_vp, C.POINTER(Params), C.POINTER(TrajInfo), _vp]),
+    "stag_md_integrate": (C.c_int, [_vp, C.POINTER(Params), _vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int),
+                                    _vp]),
     "stag_remez": (C.c_int, [C.c_double, C.c_double, C.c_double, C.c_int, C.POINTER(Rational),
                              _dp]),
     "stag_apply_M_noalloc": (C.c_int, [C.POINTER(C.c_int), _vp, C.c_double, _vp, _vp, _vp]),
@@ -364,6 +366,16 @@ class Lattice:
         info = TrajInfo()
         self._chk(lib().stag_md_trajectory(self._h, C.byref(params), C.byref(info), _stream()))
         return info.as_dict()
+
+    def md_integrate(self, params, phi=None):
+        """MD over params.tau from the current links and momenta with phi
+        (torch complex128 [npf, V/2, 3] or None for npf = 0) held fixed;
+        returns (cg_iters, n_force)."""
+        it = C.c_longlong(0)
+        nf = C.c_int(0)
+        self._chk(lib().stag_md_integrate(self._h, C.byref(params), _ptr(phi), C.byref(it), C.byref(nf),
+                                          _stream()))
+        return it.value, nf.value
 
 
 def make_params(beta, mass, tau, nsteps, integrator, hb, act, force, npf=1, tol_md=1e-10,

@@ -157,3 +157,59 @@ def test_no_metropolis_keeps_the_md_result(S, rationals):
                                        no_metropolis=1))
     assert ig["accepted"] == 1 and abs(ig["dH"] - io["dH"]) < 1e-8
     assert np.abs(L.store_gauge() - Um).max() < 1e-11
+
+
+def _md_params(S, rationals, mode, integrator=1, nsteps=4, tau=0.5, ngauge=0, oracle=False):
+    hb, act = _rats(rationals, "d6_1e-2")
+    mk = O.make_params if oracle else S.make_params
+    kw = dict(tol_md=1e-12, tol_metro=1e-12, ngauge=ngauge)
+    if not oracle:
+        kw.update(mode_md=mode, mode_metro=mode)
+    return mk(5.3, 0.2, tau, nsteps, integrator, hb, act, act, **kw)
+
+
+@pytest.mark.parametrize("ngauge", [0, 2])
+def test_md_integrate_matches_oracle(S, rationals, ngauge):
+    """Molecular dynamics alone from given links, momenta and pseudofermion:
+    links and momenta as the oracle's (FP64)."""
+    dims = (4, 4, 4, 4)
+    U = synth.near_unit_links(dims, 0.3, 12)
+    W = synth.gaussian_momenta(dims, 13)
+    phi = synth.gaussian_vector(dims, 14)[None]
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    L.load_momenta(W)
+    it, nf = L.md_integrate(_md_params(S, rationals, S.SOLVE_F64, ngauge=ngauge),
+                            torch.from_numpy(np.ascontiguousarray(phi)).cuda())
+    Uo, Wo, ito, nfo, st = O.md_integrate(dims, U, W, phi, _md_params(S, rationals, 0, ngauge=ngauge, oracle=True))
+    assert st == 0 and nf == nfo == 9
+    assert np.abs(L.store_gauge() - Uo).max() < 1e-10
+    assert np.abs(L.store_momenta() - Wo).max() < 1e-9
+
+
+def test_md_reversibility_fp64_and_mixed(S, rationals):
+    """Sec. 4.4: integrate to tau, flip the momenta, integrate back.  FP64:
+    back to the start to rounding; mixed (FP32 gauge force): a small, larger
+    violation, as the paper reports for single-precision gauge updates."""
+    dims = (6, 4, 6, 10)
+    U = synth.near_unit_links(dims, 0.3, 15)
+    W = synth.gaussian_momenta(dims, 16)
+    phi = torch.from_numpy(np.ascontiguousarray(synth.gaussian_vector(dims, 17)[None])).cuda()
+    dof = 4 * 8 * synth.volume(dims)
+    dC = {}
+    for mode in (S.SOLVE_F64, S.SOLVE_MIXED):
+        L = S.Lattice(dims)
+        L.load_gauge(U)
+        L.load_momenta(W)
+        p = _md_params(S, rationals, mode)
+        L.md_integrate(p, phi)
+        assert np.abs(L.store_gauge() - U).max() > 1e-2  # it moved
+        L.load_momenta(-L.store_momenta())
+        L.md_integrate(p, phi)
+        dC[mode] = np.sqrt((np.abs(L.store_gauge() - U) ** 2).sum() / dof)
+        dM = np.sqrt(((L.store_momenta() + W) ** 2).sum() / dof)
+        if mode == S.SOLVE_F64:
+            assert dC[mode] < 1e-12 and dM < 1e-11
+        else:
+            assert dC[mode] < 1e-5 and dM < 1e-4
+    assert dC[S.SOLVE_MIXED] > dC[S.SOLVE_F64]
