@@ -616,13 +616,17 @@ def main():
     t_e2e, roof, roof_large, batch, bsolve, learned, revers = None, None, None, None, None, None, None
     link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
     if not args.no_extras:
-        # end to end through the C ABI with host buffers: H2D links, trajectory, D2H links
-        Uh = L.store_gauge()
+        # end to end through the C ABI with pinned host buffers: H2D links,
+        # trajectory (its result: dH and the accept flag come back to the
+        # host), D2H links
+        pin_in = torch.empty((4, L.V, 3, 3), dtype=torch.complex128, pin_memory=True)
+        pin_out = torch.empty((4, L.V, 3, 3), dtype=torch.complex128, pin_memory=True)
+        L.store_gauge(out=pin_in.numpy())
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        L.load_gauge(Uh)
+        L.load_gauge(pin_in.numpy())
         L.md_trajectory(_params(stag, rat_hb, rat_act, mode, 999, seeds["rng"]))
-        Uh = L.store_gauge()
+        L.store_gauge(out=pin_out.numpy())
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
         roof = hop_roofline(stag, torch, DIMS)

@@ -262,8 +262,11 @@ class Lattice:
         else:
             self._chk(lib().stag_load_gauge(self._h, _ptr(U), 1, _stream()))
 
-    def store_gauge(self):
-        U = np.zeros((4, self.V, 3, 3), np.complex128)
+    def store_gauge(self, out=None):
+        """Canonical links to a host array (new, or `out`: complex128
+        [4,V,3,3], e.g. a view of pinned memory)."""
+        U = np.zeros((4, self.V, 3, 3), np.complex128) if out is None else out
+        assert U.shape == (4, self.V, 3, 3) and U.dtype == np.complex128 and U.flags.c_contiguous
         self._chk(lib().stag_store_gauge(self._h, U.ctypes.data_as(_vp), 0, _stream()))
         return U
 
