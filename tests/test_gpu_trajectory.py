@@ -213,3 +213,25 @@ def test_md_reversibility_fp64_and_mixed(S, rationals):
         else:
             assert dC[mode] < 1e-5 and dM < 1e-4
     assert dC[S.SOLVE_MIXED] > dC[S.SOLVE_F64]
+
+
+def test_trajectory_full_size_32x32x32x8_f64(S):
+    """The bench's lattice, mass and rationals (degree 15 on [1e-5, 64]), one
+    short leapfrog step (tau 0.005) from the smooth start, FP64 mode: heatbath, actions,
+    forces, updates and the Metropolis decision against the oracle at full
+    size (the oracle's solves on the smooth field take seconds)."""
+    dims = (32, 32, 32, 8)
+    a = S.remez(-0.5, 1e-5, 64.0, 15)[:3]
+    h = S.remez(0.25, 1e-5, 64.0, 15)[:3]
+    U = synth.near_unit_links(dims, 0.3, 1)
+    po = O.make_params(5.5, 0.0075, 0.005, 1, 0, h, a, a, tol_md=1e-10, tol_metro=1e-10, seed=3, traj=4)
+    Uo, io, st = O.trajectory(dims, U, po)
+    assert st == 0 and io["accepted"] == 1  # a step short enough to be kept: the links moved
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    ig = L.md_trajectory(S.make_params(5.5, 0.0075, 0.005, 1, 0, h, a, a, tol_md=1e-10, tol_metro=1e-10,
+                                       mode_md=S.SOLVE_F64, mode_metro=S.SOLVE_F64, seed=3, traj=4))
+    assert ig["accepted"] == io["accepted"]
+    assert abs(ig["H0"] - io["H0"]) < 1e-10 * abs(io["H0"])
+    assert abs(ig["dH"] - io["dH"]) < 1e-6
+    assert np.abs(L.store_gauge() - Uo).max() < 1e-10
