@@ -217,3 +217,25 @@ def test_learned_mode_multishift(S):
         assert info.true_resid[k] <= tol
         assert rel(host(sols[k]), xo[k]) < 1e-7
     assert info.iters_shift[1] > 0  # the flexible CG ran on shift 1
+
+
+def test_learned_mode_trajectory(S, rationals):
+    """A 4^4 trajectory whose MD force solves use SOLVE_LEARNED (lightest
+    pole by the network-preconditioned flexible CG): same decision and dH as
+    the oracle within the mixed-mode tolerance, since every solve still meets
+    1e-10 in FP64."""
+    dims = (4, 4, 4, 4)
+    h, r = rationals["p+1/4_d8_1e-3"], rationals["p-1/2_d8_1e-3"]
+    hb, act = (h["a0"], h["a"], h["b"]), (r["a0"], r["a"], r["b"])
+    U = synth.near_unit_links(dims, 0.3, 0)
+    po = O.make_params(5.3, 0.1, 1.0, 10, 0, hb, act, act, tol_md=1e-10, tol_metro=1e-10, seed=11, traj=0)
+    _, io, st = O.trajectory(dims, U, po)
+    assert st == 0
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    net = S.Net(L, seed=6)
+    net.attach()
+    ig = L.md_trajectory(S.make_params(5.3, 0.1, 1.0, 10, 0, hb, act, act, tol_md=1e-10, tol_metro=1e-10,
+                                       mode_md=S.SOLVE_LEARNED, mode_metro=S.SOLVE_MIXED, seed=11, traj=0))
+    assert ig["accepted"] == io["accepted"]
+    assert abs(ig["dH"] - io["dH"]) < 1e-6 * max(1.0, abs(io["dH"]))
