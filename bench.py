@@ -512,6 +512,9 @@ def main():
                     help="skip the e2e and roofline measurements (profiling runs)")
     ap.add_argument("--roofline-only", action="store_true",
                     help="only time the FP32 hop on the roofline lattice")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="one mixed multi-shift solve of the workload's rational on the smooth "
+                         "32^3x8 start (few launches: for kernel profiles)")
     ap.add_argument("--roof-dims", default="64,64,64,16",
                     help="lattice of the large-lattice hop roofline, e.g. 48,48,48,16")
     ap.add_argument("--therm", type=int, default=THERM,
@@ -529,6 +532,21 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     NSTEPS = args.nsteps
+    if args.solve_only:
+        import torch
+        from paper_1106_5673_gb300 import stag, synth
+        _, _, b, _ = stag.remez(-0.5, LO, HI, DEG)
+        L = stag.Lattice(DIMS)
+        L.load_gauge(synth.near_unit_links(DIMS, 0.3, 1))
+        x = torch.from_numpy(synth.gaussian_vector(DIMS, 3)).cuda()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = L.multishift_solve(MASS, b, x, tol=TOL, mode=stag.SOLVE_MIXED)
+        torch.cuda.synchronize()
+        print(json.dumps({"solve_only": {"seconds": time.perf_counter() - t0, "iters": info.iters,
+                                         "refine_iters": list(info.refine_iters[:len(b)]),
+                                         "max_true_resid": max(info.true_resid[:len(b)])}}))
+        return 0
     if args.roofline_only:
         import torch
         from paper_1106_5673_gb300 import stag

@@ -43,7 +43,7 @@ STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
 }
 
 template <int LP>
-__global__ void __launch_bounds__(256) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
+__global__ void __launch_bounds__(256, 4) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
                                                  float2* __restrict__ T, size_t stride, BCGState* st) {
     // a stop requested by the previous iteration takes effect here, after that
     // iteration's vector update
@@ -213,7 +213,7 @@ __global__ void k_b_D(long n, size_t stride, const float2* __restrict__ R, float
 // expansion, beta_k and the parking; CD applies r -= alpha w, x += alpha p and
 // (for right-hand sides still active) p = r + beta p.
 template <int LP>
-__global__ void __launch_bounds__(256) k_b_B3(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
+__global__ void __launch_bounds__(256, 4) k_b_B3(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
                                                   const float2* __restrict__ P, const float2* __restrict__ R,
                                                   float2* __restrict__ W, size_t stride, BCGState* st,
                                                   double* partials, double* gpart, unsigned int* counter) {
