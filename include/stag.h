@@ -162,7 +162,9 @@ int stag_ctx_device_bytes(const stag_ctx *ctx, size_t *bytes);
 int stag_ctx_launch_count(const stag_ctx *ctx, long long *n);
 /* Autotuner: times the hop kernels for 64, 128 and 256 threads per block for
  * each link precision (FP64, FP32, BF16, float-float; CUDA events after
- * warm-up) on the loaded gauge field and keeps the fastest for this context;
+ * warm-up, best of three timings of ten launches) on the loaded gauge field
+ * and keeps the fastest for this context, unless it beats 128 by less than
+ * 3 % (then 128);
  * tpb_out (nullable, 4 ints) receives the choice.  The first solve on a
  * context runs it automatically unless the environment sets STAG_AUTOTUNE=0.
  * Synchronises. */
