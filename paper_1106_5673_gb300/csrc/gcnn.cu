@@ -333,6 +333,8 @@ int net_create(stag_ctx* ctx, unsigned seed, stag_net** out) {
     if (e == cudaSuccess) e = cudaMallocHost(&net->hsc, sizeof(double) * 16);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        net->ctx = nullptr;  // not attached: net_destroy frees what was allocated
+        net_destroy(net);
         stag_fail(ctx, STAG_ERR_OOM, "network allocation");
         return STAG_ERR_OOM;
     }
@@ -358,7 +360,12 @@ int net_create(stag_ctx* ctx, unsigned seed, stag_net** out) {
         cudaMemcpy(net->w32[l], h.data(), sizeof(float2) * net->nw[l], cudaMemcpyHostToDevice);
         k_gc_tobf16<<<nblocks(net->nw[l], 128), 128>>>(net->nw[l], net->w32[l], net->w16[l]);
     }
-    if (cudaDeviceSynchronize() != cudaSuccess) return stag_cuda_check(ctx, cudaGetLastError(), "network init");
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        const int st = stag_cuda_check(ctx, cudaGetLastError(), "network init");
+        net->ctx = nullptr;
+        net_destroy(net);
+        return st;
+    }
     *out = net;
     return STAG_OK;
 }
