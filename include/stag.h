@@ -240,13 +240,19 @@ int stag_dslash_batch(int nlat, stag_ctx *const *ctxs, const void *const *in, vo
 /* Solves (M_ee + shifts[k]) x_k = src for k < n (1 <= n <= STAG_MAXSHIFT,
  * shifts >= 0) from x = 0 with the shifted CG, stopping shift k when its
  * residual falls below tol*|src|.  src and sols[k] are FP64 device vectors
- * (canonical complex128, even sites); sols[k] may alias nothing else.
- * mode: STAG_SOLVE_F64, or STAG_SOLVE_MIXED(_BF16): FP32 multi-shift with FP64
- * reliable updates of the base residual, then an FP64-reliable-update CG per
- * shift started from x_k until the FP64 true residual meets tol.  The true
- * residual of every shift is computed in FP64 and returned in info.
- * Synchronises (reads convergence flags).  Returns STAG_ERR_NOCONV if any
- * shift misses tol within maxit iterations. */
+ * (canonical complex128, even sites); sols[k] (nullable entries, sols itself
+ * nullable) may alias nothing else.  mode (see STAG_SOLVE_*):
+ *  F64, F64FF   the shifted CG in FP64 (or float-float) arithmetic; a shift
+ *               whose FP64 true residual is still above tol when its
+ *               recursion stops resumes the recursion with a tighter target
+ *               (or, if it was frozen earlier, is refined as below);
+ *  MIXED(_BF16) the shifted CG in FP32 to max(tol, 1e-6), then every shift
+ *               above tol refined from x_k by one batched FP32 CG (all such
+ *               shifts in the same kernels) with FP64 reliable updates;
+ *  LEARNED      see the enum.
+ * The true residual of every shift is computed FP64-accurately and returned
+ * in info.  Synchronises (reads convergence flags).  Returns STAG_ERR_NOCONV
+ * if any shift misses tol within maxit iterations. */
 int stag_multishift_solve(stag_ctx *ctx, double mass, int n, const double *shifts,
                           const double *src, double *const *sols, double tol, int maxit,
                           int mode, stag_solve_info *info, void *stream);
@@ -255,8 +261,9 @@ int stag_multishift_solve(stag_ctx *ctx, double mass, int n, const double *shift
  * (1 <= nsys <= STAG_MAXRHS, e.g. the pseudofermions of one force
  * evaluation) and the same n shifts, advancing all systems together: the hop
  * kernels load each link once for a group of systems.  Each system stops on
- * its own; mixed modes refine every (system, shift) above tolerance in
- * batches of STAG_MAXSHIFT.  sols[r*n + k] (nullable entries; sols itself
+ * its own; every (system, shift) whose FP64-accurate true residual is above
+ * tolerance is then refined by the batched CG, STAG_MAXSHIFT pairs at a time
+ * (modes F64, F64FF, MIXED, MIXED_BF16; not LEARNED).  sols[r*n + k] (nullable entries; sols itself
  * nullable) receive the FP64 solutions; infos (nullable) holds nsys entries.
  * Synchronises.  Errors as stag_multishift_solve. */
 int stag_multishift_solve_multi(stag_ctx *ctx, double mass, int nsys, int n, const double *shifts,
