@@ -60,3 +60,23 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
         steps, warmup, gpus, ref_iters = 1, 0, 2, 10
     assert bench.reference_arm(A()) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """`bench.py --impl reference` on rank 0: one JSON line timing the oracle
+    on a bounded sample of the workload, with the contract's keys and the
+    same metric, unit and config as the library's arm."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "0")
+
+    class A:
+        steps, warmup, gpus, ref_iters = 1, 0, 1, 1000
+    assert bench.reference_arm(A()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench._metric()
+    assert line["unit"] == "s/trajectory" and line["higher_is_better"] is False
+    assert line["value"] > 0 and line["config"] == bench.workload_config()
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
