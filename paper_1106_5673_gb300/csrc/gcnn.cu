@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(TPB) k_gc_wgrad(Geom g, const float4* __restri
             }
 #pragma unroll
             for (int o = 0; o < COUT; o++) {
-                double re = warp_sum((double)d[o].x), im = warp_sum((double)d[o].y);
+                // warp level in FP32 (FP64 shuffles are slow on GB300), FP64 across warps
+                const double re = warp_sum_f(d[o].x), im = warp_sum_f(d[o].y);
                 if (lane == 0) {
                     atomicAdd(&acc_s[((o * CIN + i) * GC_TAPS + t) * 2], re);
                     atomicAdd(&acc_s[((o * CIN + i) * GC_TAPS + t) * 2 + 1], im);
