@@ -55,3 +55,28 @@ def test_host_remez_matches_oracle(stag, rationals, key):
 def test_host_remez_degree_zero(stag):
     a0, a, b, err = stag.remez(-0.5, 0.01, 5.0, 0)
     assert a == [] and abs(a0 - 2 / (0.01 ** 0.5 + 5 ** 0.5)) < 1e-15
+
+
+def test_every_exported_entry_point_is_declared():
+    """Every stag_* function the sources define with C linkage is declared in
+    the header (the boundary is the header, nothing more)."""
+    csrc = os.path.join(ROOT, "paper_1106_5673_gb300", "csrc")
+    defined = set()
+    for f in os.listdir(csrc):
+        if f.endswith((".cu", ".cpp")):
+            txt = open(os.path.join(csrc, f)).read()
+            defined |= set(re.findall(r"^(?:extern \"C\" )?int (stag_\w+)\(", txt, re.M))
+    internal = open(os.path.join(csrc, "stag_internal.h")).read()
+    defined = {n for n in defined if not re.search(r"\bint %s\(" % n, internal)}  # C++ helpers
+    declared = set(_declared("stag.h"))
+    assert defined, "no entry points found"
+    assert defined <= declared, sorted(defined - declared)
+
+
+def test_build_compiles_every_source():
+    from paper_1106_5673_gb300 import build
+    csrc = os.path.join(ROOT, "paper_1106_5673_gb300", "csrc")
+    srcs = sorted(f for f in os.listdir(csrc) if f.endswith((".cu", ".cpp")))
+    assert sorted(build.SOURCES) == srcs
+    hdrs = sorted(f for f in os.listdir(csrc) if f.endswith((".cuh", ".h")))
+    assert sorted(build.HEADERS) == hdrs
