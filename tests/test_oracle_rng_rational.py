@@ -1,4 +1,6 @@
 """Pins of the oracle's random numbers and of its Remez rational functions."""
+import os
+
 import numpy as np
 import pytest
 
@@ -9,6 +11,27 @@ from tests import helpers as H
 
 
 # ---------------------------------------------------------------- Philox / Box-Muller
+
+def _kat_vectors():
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                w = [int(x, 16) for x in line.split()]
+                rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+def test_philox_known_answer_vectors():
+    """Philox4x32-10 reproduces the published known-answer vectors (Salmon et
+    al., SC'11; the test vectors distributed with their Random123 library):
+    a wrong multiplier, Weyl constant, word order or key schedule fails here."""
+    rows = _kat_vectors()
+    assert len(rows) == 3
+    for ctr, key, want in rows:
+        assert O.philox(ctr, key) == want, (ctr, key)
+
 
 def _uniforms(n, key=(7, 9)):
     u = np.array([O.uniform_pair((5, 0, i, 0), key) for i in range(n)])
