@@ -35,9 +35,9 @@ BETA, MASS, TAU, NSTEPS, DEG, LO, HI, TOL = 5.5, 0.0075, 1.0, 20, 15, 1e-5, 64.0
 ROOF_DIMS = (64, 64, 64, 16)  # working set >= 4x L2 for the Dslash roofline
 THERM, THERM_STEPS = 60, 40   # pure-gauge thermalisation: trajectories, Omelyan steps (tau = 1)
 # DRAM bytes (read + write) per output site of k_hop<float,1> from one ncu
-# capture at 48^3x16 (profiles/k_hop_f32_48x48x48x16.md): 383.8 MB / 884736
-# sites; traffic grows in proportion to the sites, so it is scaled to the
-# roofline lattice by Vh.  Algorithmic bytes per site: 600.
+# capture at 48^3x16: 383.8 MB / 884736 sites; traffic grows in proportion to
+# the sites, so it is scaled to the roofline lattice by Vh.  Algorithmic
+# bytes per site: 600.
 HOP_TRAFFIC_PER_SITE = 433.8
 # total multi-shift iterations of one FP64 trajectory of this workload, as
 # counted by the library's FP64 path (identical to the oracle's recursion);

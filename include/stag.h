@@ -124,7 +124,13 @@ typedef struct {
     int solve_mode_metro;       /* STAG_SOLVE_* for heatbath and action solves      */
     int maxit;                  /* iteration cap of every solve                     */
     uint32_t seed, traj;        /* Philox key (seed, traj)                          */
-    int use_graphs;             /* capture the MD loop's force/update steps         */
+    int use_graphs;             /* 1: every solver iteration chunk (16 iterations
+                                   of a shifted or batched CG) runs as a cached
+                                   CUDA graph, replayed between the host's
+                                   convergence polls; 0: the same kernels are
+                                   launched one by one.  Forces, updates and the
+                                   Hamiltonian are launched kernel by kernel
+                                   either way.  Results are identical.             */
     int ngauge;                 /* 0: one time scale.  n > 0: multi-step scheme
                                    (Sec. 2.1, Sexton-Weingarten): the integrator
                                    moves P with the fermion force only, and each
@@ -212,7 +218,9 @@ int stag_apply_M(stag_ctx *ctx, double mass, const void *in_even, void *out_even
  * 2^17 sites (6 MiB), resident on every device that loads the library until
  * exit; lattices with V/2 > 2^17 (larger than 32^3 x 8) are rejected with
  * STAG_ERR_ARG.  The first call on a device looks up the array's address
- * (set-up); make that first call before any stream capture.  All calls share
+ * (set-up) and keeps it for the life of the process; make that first call
+ * before any stream capture, and do not call this function on a device after
+ * cudaDeviceReset (the kept address is then stale).  All calls share
  * the array: calls whose kernels overlap on the GPU race.  Returns STAG_OK,
  * STAG_ERR_ARG (bad sizes or pointers) or STAG_ERR_CUDA; there is no error
  * string, since there is no context.  Asynchronous on `stream`. */

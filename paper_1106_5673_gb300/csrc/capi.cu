@@ -88,6 +88,7 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
     stag_ctx* ctx = new stag_ctx();
     memset(ctx->err, 0, sizeof ctx->err);
     for (int m = 0; m < 4; m++) ctx->g.L[m] = dims[m];
+    ctx->use_graphs = 1;
     ctx->g.V = (int)V;
     ctx->g.Vh = (int)(V / 2);
     ctx->g.Lx2 = dims[0] / 2;
@@ -462,7 +463,11 @@ int stag_md_trajectory(stag_ctx* ctx, const stag_params* p, stag_traj_info* out,
     if (!p || !out) return stag_fail(ctx, STAG_ERR_ARG, "null params or output");
     int st = check_params(ctx, p);
     if (st) return st;
-    return rhmc_trajectory(ctx, p, out, S(stream));
+    const int graphs = ctx->use_graphs;
+    ctx->use_graphs = p->use_graphs ? 1 : 0;
+    st = rhmc_trajectory(ctx, p, out, S(stream));
+    ctx->use_graphs = graphs;
+    return st;
 }
 
 int stag_md_integrate(stag_ctx* ctx, const stag_params* p, const double* phi, long long* cg_iters, int* n_force,
@@ -475,7 +480,11 @@ int stag_md_integrate(stag_ctx* ctx, const stag_params* p, const double* phi, lo
     if (p->npf > 0 && !phi) return stag_fail(ctx, STAG_ERR_ARG, "null pseudofermions");
     long long it = 0;
     int nf = 0;
-    if ((st = md_integrate_public(ctx, p, (const double2*)phi, &it, &nf, S(stream)))) return st;
+    const int graphs = ctx->use_graphs;
+    ctx->use_graphs = p->use_graphs ? 1 : 0;
+    st = md_integrate_public(ctx, p, (const double2*)phi, &it, &nf, S(stream));
+    ctx->use_graphs = graphs;
+    if (st) return st;
     STAG_CUDA(ctx, cudaStreamSynchronize(S(stream)));
     if (cg_iters) *cg_iters = it;
     if (n_force) *n_force = nf;

@@ -77,12 +77,14 @@ extern "C" int stag_apply_M_noalloc(const int dims[4], const double* links, doub
     if (!dims || !links || !in_even || !out_even) return STAG_ERR_ARG;
     if (((uintptr_t)links | (uintptr_t)in_even | (uintptr_t)out_even) & 15u) return STAG_ERR_ARG;
     if (in_even == out_even) return STAG_ERR_ARG;
-    long V = 1;
+    // each extent is bounded before it is multiplied in, so the product can
+    // neither overflow nor wrap below the limit
+    long long V = 1;
     for (int m = 0; m < 4; m++) {
-        if (dims[m] < 2 || (dims[m] & 1)) return STAG_ERR_ARG;
+        if (dims[m] < 2 || (dims[m] & 1) || dims[m] > 2 * STAG_NOALLOC_MAX_VH) return STAG_ERR_ARG;
         V *= dims[m];
+        if (V / 2 > STAG_NOALLOC_MAX_VH) return STAG_ERR_ARG;  // beyond the fixed scratch array
     }
-    if (V / 2 > STAG_NOALLOC_MAX_VH) return STAG_ERR_ARG;  // beyond the fixed scratch array
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();

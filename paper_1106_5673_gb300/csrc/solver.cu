@@ -574,10 +574,11 @@ static cudaError_t persist_links(stag_ctx* ctx, cudaGraph_t graph) {
 
 template <typename F>
 int run_chunk(stag_ctx* ctx, const std::string& key, int nkernels, F fn, cudaStream_t s) {
-    static int use_graphs = -1;
-    if (use_graphs < 0) use_graphs = env_int("STAG_GRAPHS", 1);
+    // STAG_GRAPHS=0 in the environment switches graphs off for the process
+    static int env_graphs = -1;
+    if (env_graphs < 0) env_graphs = env_int("STAG_GRAPHS", 1);
     ctx->nlaunch += nkernels;
-    if (!use_graphs) {
+    if (!env_graphs || !ctx->use_graphs) {
         fn(s);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return stag_cuda_check(ctx, e, key.c_str());

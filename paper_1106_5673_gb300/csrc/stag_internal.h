@@ -104,6 +104,7 @@ struct stag_ctx {
     int tpb[4];         // tuned threads per block of the hop kernels, per link precision (0: default)
     int tuned;
     stag_net* net;      // preconditioner of STAG_SOLVE_LEARNED (borrowed)
+    int use_graphs;     // 1: solver iteration chunks run as cached CUDA graphs
 };
 
 // threads per block of the hop kernels for link precision lp (autotuned, else 128)

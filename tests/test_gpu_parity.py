@@ -305,3 +305,22 @@ def test_error_codes(S):
     # the context stays usable afterwards
     _, info = L.multishift_solve(0.1, [0.0, 0.1], b, tol=1e-10)
     assert info.status == 0
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("bad", [float("nan"), float("inf")])
+def test_nonfinite_source_is_reported(S, mode, bad):
+    """A source with one non-finite entry (injected on the host) makes every
+    solver mode return STAG_ERR_NONFINITE instead of a result, and the
+    context stays usable."""
+    dims = (6, 4, 6, 10)
+    L = S.Lattice(dims)
+    L.load_gauge(synth.near_unit_links(dims, 0.3, 3))
+    b = synth.gaussian_vector(dims, 4)
+    bad_b = b.copy()
+    bad_b[17, 1] = complex(bad, 0.0)
+    with pytest.raises(S.StagError) as e:
+        L.multishift_solve(0.1, [0.0, 0.05, 0.5], dev(bad_b), tol=1e-10, mode=mode)
+    assert e.value.code == S.ERR_NONFINITE
+    sols, info = L.multishift_solve(0.1, [0.0, 0.05, 0.5], dev(b), tol=1e-10, mode=mode)
+    assert info.status == 0 and max(info.true_resid[:3]) <= 1e-10
