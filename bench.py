@@ -10,7 +10,14 @@ FP64 link and momentum updates, Metropolis):
   1 + rank), then THERM pure-gauge molecular-dynamics trajectories at the same
   beta (untimed), which bring the plaquette from 0.78 to the rough, confined
   regime (~0.50) whose Dirac spectrum has the near-zero modes that set the
-  solver cost of the paper's workloads.
+  solver cost of the paper's workloads, then EQUIL RHMC trajectories with the
+  Metropolis test that bring the fermion part to equilibrium (untimed).
+After the timed region: the same number of trajectories end to end through
+the C ABI from pinned host buffers (e2e), the next trajectory (or --chain K of
+them) from the same start in FP64, float-float FP64 and the timed form, one
+more trajectory under CUPTI for the kernel table, the hop roofline and the
+other measurements, and the FP64 oracle's cost on the host (one core and
+every core).
 Multi-GPU: the path does not shard (one lattice per GPU), so N ranks run N
 independent replicas (different seeds) and the value is the whole-job
 seconds per trajectory: max-over-ranks time / (steps * N).
@@ -34,6 +41,7 @@ DIMS = (32, 32, 32, 8)
 BETA, MASS, TAU, NSTEPS, DEG, LO, HI, TOL = 5.5, 0.0075, 1.0, 20, 15, 1e-5, 64.0, 1e-10
 ROOF_DIMS = (64, 64, 64, 16)  # working set >= 4x L2 for the Dslash roofline
 THERM, THERM_STEPS = 60, 40   # pure-gauge thermalisation: trajectories, Omelyan steps (tau = 1)
+EQUIL = 10                    # RHMC trajectories with Metropolis after it (fermion equilibration)
 # DRAM bytes (read + write) per output site of k_hop<float,1> from one ncu
 # capture at 48^3x16: 383.8 MB / 884736 sites; traffic grows in proportion to
 # the sites, so it is scaled to the roofline lattice by Vh.  Algorithmic
@@ -74,7 +82,7 @@ def whole_job_value(t_max, steps, world):
     return t_max / (steps * world)
 
 
-def workload_config(therm=THERM, world=1):
+def workload_config(therm=THERM, world=1, equil=EQUIL):
     """The workload as both arms report it (config)."""
     return {"workload": WORKLOAD, "lattice": list(DIMS), "beta": BETA, "mass": MASS,
             "integrator": "omelyan", "nsteps": NSTEPS, "tau": TAU, "rational_degree": DEG,
@@ -82,7 +90,9 @@ def workload_config(therm=THERM, world=1):
             "parallelism": "replicas" if world > 1 else "single",
             "start": {"links": "exp(i 0.3 H)",
                       "thermalisation": "%d pure-gauge MD trajectories (tau 1, %d Omelyan steps, "
-                                        "no Metropolis)" % (therm, THERM_STEPS)},
+                                        "no Metropolis)" % (therm, THERM_STEPS),
+                      "equilibration": "%d RHMC trajectories with Metropolis (MD solves 1e-7, "
+                                       "Metropolis solves 1e-10)" % equil},
             "l2": "working set > L2 (links fp64+fp32+bf16 ~176 MB, solver vectors ~200 MB)"}
 
 
@@ -174,6 +184,60 @@ def hop_roofline(stag, torch, dims, nrep=30):
     Vh = int(np.prod(dims)) // 2
     return {"seconds": t, "bytes": 600.0 * Vh, "gbs": 600.0 * Vh / t / 1e9,
             "gflops": 570.0 * Vh / t / 1e9, "dims": list(dims)}
+
+
+def equilibrate(stag, L, rat_hb, rat_act, seed, ntraj):
+    """RHMC trajectories with the Metropolis test (mixed mode, MD solves to
+    1e-7, Metropolis solves to 1e-10) after the pure-gauge thermalisation, so
+    that the fermion part of the action is in equilibrium too before anything
+    is timed; returns the list of (dH, accepted)."""
+    out = []
+    for i in range(ntraj):
+        p = stag.make_params(BETA, MASS, TAU, NSTEPS, stag.INT_OMELYAN, rat_hb, rat_act, rat_act,
+                             tol_md=1e-7, tol_metro=TOL, mode_md=stag.SOLVE_MIXED,
+                             mode_metro=stag.SOLVE_MIXED, seed=seed, traj=10000 + i)
+        info = L.md_trajectory(p)
+        out.append((info["dH"], info["accepted"]))
+    return out
+
+
+def compare_chain(stag, torch, L, rat_hb, rat_act, seed, traj0, ntraj, mode, forms):
+    """Trajectories traj0 .. traj0+ntraj-1 of the timed chain, each run from
+    the same start configuration and random numbers in every solver form
+    (FP64, float-float FP64, the timed mode); the chain continues with the
+    timed mode's result.  Per trajectory: dH, accept and seconds per form."""
+    rows = []
+    for i in range(ntraj):
+        Ustart = L.store_gauge()
+        row = {"traj": traj0 + i}
+        for name, m in forms:
+            L2 = stag.Lattice(DIMS)
+            L2.load_gauge(Ustart)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = L2.md_trajectory(_params(stag, rat_hb, rat_act, m, traj0 + i, seed))
+            torch.cuda.synchronize()
+            row[name] = {"s": time.perf_counter() - t0, "dH": info["dH"], "accepted": info["accepted"],
+                         "cg_iters": info["cg_iters"]}
+            if m == mode:
+                Unext = L2.store_gauge()
+            L2.close()
+        L.load_gauge(Unext)
+        rows.append(row)
+    names = [n for n, _ in forms]
+    summ = {"trajectories": ntraj,
+            "s_per_traj": {n: statistics.mean(r[n]["s"] for r in rows) for n in names},
+            "accept_sequences": {n: [r[n]["accepted"] for r in rows] for n in names}}
+    if "f64" in names:
+        for n in names:
+            if n != "f64":
+                summ["max_abs_ddH_%s_vs_f64" % n] = max(abs(r[n]["dH"] - r["f64"]["dH"]) for r in rows)
+                summ["same_accepts_%s_vs_f64" % n] = all(r[n]["accepted"] == r["f64"]["accepted"]
+                                                         for r in rows)
+    if "f64" in names:
+        summ["f64_cg_iters"] = statistics.mean(r["f64"]["cg_iters"] for r in rows)
+    summ["rows"] = rows
+    return summ
 
 
 def thermalise(stag, L, rat, seed, ntraj=THERM, beta=BETA):
@@ -428,6 +492,29 @@ def _kernel_name(k):
     return "".join(out)
 
 
+def cpu_samples_all_cores(iters_per_traj, n_force, nrep=1):
+    """nrep cpu_sample runs with the oracle's all-cores build (OpenMP over
+    its site loops, identical arithmetic), in a child process with one thread
+    per host core; the start links are the smooth start of the workload (the
+    sample's cost does not depend on them).  Returns the list of samples."""
+    ncores = os.cpu_count() or 1
+    code = ("import json, sys; sys.path.insert(0, %r); import bench, oracle as O; "
+            "from paper_1106_5673_gb300 import synth; O.build(openmp=True); "
+            "g = json.load(open(%r))['p-1/2_d15_1e-5']; "
+            "U = synth.near_unit_links(bench.DIMS, 0.3, 1); "
+            "print(json.dumps([bench.cpu_sample(U, (g['a0'], g['a'], g['b']), %d, %d) for _ in range(%d)]))"
+            % (ROOT, os.path.join(ROOT, "tests", "golden", "rationals.json"), iters_per_traj, n_force, nrep))
+    env = dict(os.environ, ORACLE_OPENMP="1", OMP_NUM_THREADS=str(ncores))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("oracle all-cores sample failed: %s" % r.stderr.strip()[-300:])
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    for o in out:
+        o["cores"] = ncores
+        o["sample"] = o["sample"].replace("on 1 host core", "on %d host cores (OpenMP build)" % ncores)
+    return out
+
+
 def cpu_sample(U, rat_act, iters_per_traj, n_force):
     """The FP64 oracle on the host: a bounded sample of the trajectory's work,
     scaled to seconds per trajectory."""
@@ -465,26 +552,18 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from paper_1106_5673_gb300 import synth
-    # the oracle's own Remez output (written by tests/golden/make_rationals.py)
-    with open(os.path.join(ROOT, "tests", "golden", "rationals.json")) as f:
-        gold = json.load(f)
-    r = gold["p-1/2_d15_1e-5"]
-    rat = (r["a0"], r["a"], r["b"])
     iters = REF_ITERS_PER_TRAJ or args.ref_iters
-    U = synth.near_unit_links(DIMS, 0.3, 1)
-    vals = []
-    for i in range(args.warmup + args.steps):
-        s = cpu_sample(U, rat, iters, 2 * NSTEPS + 1)
-        if i >= args.warmup:
-            vals.append(s)
+    # every host core: the oracle's OpenMP build in a child process, with the
+    # oracle's own Remez output (tests/golden/rationals.json, written by
+    # tests/golden/make_rationals.py)
+    vals = cpu_samples_all_cores(iters, 2 * NSTEPS + 1, args.warmup + args.steps)[args.warmup:]
     v = statistics.mean(x["value"] for x in vals)
     line = {"impl": "reference", "metric": _metric(), "value": v, "unit": "s/trajectory",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(),
-            "cpu_baseline": {"value": v, "unit": "s/trajectory", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "s/trajectory", "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": "s/trajectory", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -525,8 +604,14 @@ def main():
     ap.add_argument("--kernel-table", default=None, metavar="FILE",
                     help="after the timed region, record one more trajectory with CUPTI "
                          "(torch.profiler) and write its per-kernel device-time table to FILE")
-    ap.add_argument("--with-ff", action="store_true",
-                    help="also run the float-float FP64 form in the same-start comparison")
+    ap.add_argument("--equil", type=int, default=EQUIL,
+                    help="RHMC trajectories with Metropolis after the pure-gauge thermalisation "
+                         "(fermion equilibration, untimed)")
+    ap.add_argument("--chain", type=int, default=1,
+                    help="trajectories after the timed region run from the same start in the FP64, "
+                         "float-float and timed forms (dH, accept and time per form)")
+    ap.add_argument("--no-ktable", action="store_true",
+                    help="skip the CUPTI kernel table of one extra trajectory")
     args = ap.parse_args()
     ROOF_DIMS = tuple(int(x) for x in args.roof_dims.split(","))
     if args.impl == "reference":
@@ -577,7 +662,9 @@ def main():
     L = stag.Lattice(DIMS)
     seeds = replica_seeds(rank)
     L.load_gauge(synth.near_unit_links(DIMS, 0.3, seeds["links"]))
-    plaq_start = thermalise(stag, L, rat_act, seeds["therm"], args.therm)
+    plaq_therm = thermalise(stag, L, rat_act, seeds["therm"], args.therm)
+    equil = equilibrate(stag, L, rat_hb, rat_act, seeds["rng"], args.equil)
+    plaq_start = L.plaquette()
     U0 = L.store_gauge()
 
     MODES = {"mixed": stag.SOLVE_MIXED, "f64": stag.SOLVE_F64, "ff": stag.SOLVE_F64FF,
@@ -610,43 +697,45 @@ def main():
     launches = L.launch_count() - n0
     value = whole_job_value(t, args.steps, world)
     iters_timed = sum(i["cg_iters"] for i in infos) / len(infos)
+    U_after = L.store_gauge()
+    traj_next = args.warmup + args.steps
 
-    # the plain FP64 GPU form and the float-float form of the next trajectory,
-    # from the same start with the same random numbers, beside the timed mode
-    compare = None
-    if not args.no_fp64:
-        Ustart = L.store_gauge()
-        traj = args.warmup + args.steps
-        compare = {}
-        forms = [("f64", stag.SOLVE_F64)] + ([("ff", stag.SOLVE_F64FF)] if args.with_ff else [])
-        for name, m in forms + [(args.mode, mode)]:
-            L2 = stag.Lattice(DIMS)
-            L2.load_gauge(Ustart)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            i2 = L2.md_trajectory(_params(stag, rat_hb, rat_act, m, traj, seeds["rng"]))
-            torch.cuda.synchronize()
-            compare[name] = {"s_per_traj": time.perf_counter() - t0, "cg_iters": i2["cg_iters"],
-                             "dH": i2["dH"], "accepted": i2["accepted"]}
-            L2.close()
-        compare["speedup_vs_f64"] = compare["f64"]["s_per_traj"] / value if world == 1 else None
-
-    t_e2e, roof, roof_large, batch, bsolve, learned, revers = None, None, None, None, None, None, None
+    # end to end through the C ABI, the same number of trajectories as the
+    # timed region: every step copies the links from pinned host memory to
+    # the device, runs the trajectory (its result, dH and the accept flag,
+    # comes back to the host) and copies the links back to pinned memory
+    t_e2e = None
     link_bytes = 4 * int(np.prod(DIMS)) * 9 * 16
     if not args.no_extras:
-        # end to end through the C ABI with pinned host buffers: H2D links,
-        # trajectory (its result: dH and the accept flag come back to the
-        # host), D2H links
         pin_in = torch.empty((4, L.V, 3, 3), dtype=torch.complex128, pin_memory=True)
         pin_out = torch.empty((4, L.V, 3, 3), dtype=torch.complex128, pin_memory=True)
-        L.store_gauge(out=pin_in.numpy())
+        pin_in.numpy()[...] = U0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        L.load_gauge(pin_in.numpy())
-        L.md_trajectory(_params(stag, rat_hb, rat_act, mode, 999, seeds["rng"]))
-        L.store_gauge(out=pin_out.numpy())
+        for k in range(args.steps):
+            L.load_gauge(pin_in.numpy())
+            L.md_trajectory(_params(stag, rat_hb, rat_act, mode, args.warmup + k, seeds["rng"]))
+            L.store_gauge(out=pin_out.numpy())
         torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
+        t_e2e = max_over_ranks((time.perf_counter() - t0) / args.steps, world) / world
+        L.load_gauge(U_after)
+
+    # the plain FP64 GPU form and the float-float FP64 form of the next
+    # trajectories, each from the same start with the same random numbers as
+    # the timed mode (the chain continues with the timed mode's result)
+    compare = None
+    if not args.no_fp64 and args.chain > 0:
+        forms = [("f64", stag.SOLVE_F64), ("ff", stag.SOLVE_F64FF)]
+        if args.mode not in ("f64", "ff"):
+            forms.append((args.mode, mode))
+        compare = compare_chain(stag, torch, L, rat_hb, rat_act, seeds["rng"], traj_next, args.chain, mode,
+                                forms)
+        compare["speedup_vs_f64"] = (compare["s_per_traj"]["f64"] / value) if world == 1 else None
+        if args.chain == 1:
+            compare.pop("rows")
+
+    roof, roof_large, batch, bsolve, learned, revers = None, None, None, None, None, None
+    if not args.no_extras:
         roof = hop_roofline(stag, torch, DIMS)
         roof_large = hop_roofline(stag, torch, ROOF_DIMS)
         batch = _extra(batched_hop, stag, torch)
@@ -655,18 +744,21 @@ def main():
         learned = _extra(learned_preconditioner, stag, torch, L, min(rat_act[2]))
     peak, peak_kind = _peaks()
     ktable = None
-    if args.kernel_table:
-        ktable = kernel_table(stag, torch, L, _params(stag, rat_hb, rat_act, mode, 998, seeds["rng"]),
-                              args.kernel_table)
+    if not args.no_ktable:
+        path = args.kernel_table or os.path.join(os.environ.get("TMPDIR", "/tmp"),
+                                                 "stag_kernel_table_%d.txt" % os.getpid())
+        ktable = _extra(kernel_table, stag, torch, L,
+                        _params(stag, rat_hb, rat_act, mode, 998, seeds["rng"]), path)
 
     line = {
         "metric": _metric(), "value": value, "unit": "s/trajectory", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": dict(workload_config(args.therm, world),
+        "config": dict(workload_config(args.therm, world, args.equil),
                        solver="mixed: fp32 multishift + fp64 reliable-update refinement",
-                       rational_err=[err_act, err_hb], start_plaquette=plaq_start),
+                       rational_err=[err_act, err_hb], start_plaquette=plaq_start,
+                       therm_plaquette=plaq_therm),
         # the FP32 even/odd hop that the solver kernels (k_ms_A/B3, k_b_A/B3)
         # share, on the roofline lattice (working set > 4x L2); algorithmic
         # bytes 600 per output site, traffic from the ncu capture
@@ -685,9 +777,11 @@ def main():
             "gflops": roof["gflops"]},
         "e2e": None if t_e2e is None else {
             "value": t_e2e, "unit": "s/trajectory", "h2d_bytes_per_step": link_bytes,
-            "d2h_bytes_per_step": link_bytes},
+            "d2h_bytes_per_step": link_bytes, "steps": args.steps},
         "gpu_launches": launches,
         "clocks": ck,
+        "equilibration": {"trajectories": args.equil, "dH": [round(d, 4) for d, _ in equil],
+                          "accepted": [a_ for _, a_ in equil]},
         "trajectories": [{k: i[k] for k in ("dH", "accepted", "plaq", "cg_iters", "n_force",
                                              "t_md", "t_total")} for i in infos],
         "mode": args.mode,
@@ -700,8 +794,11 @@ def main():
         "reversibility": revers,
     }
     if rank == 0 and world == 1 and not args.no_cpu:
-        iters = compare["f64"]["cg_iters"] if compare else (REF_ITERS_PER_TRAJ or args.ref_iters)
-        line["cpu_baseline"] = cpu_sample(U0, rat_act, iters, infos[0]["n_force"])
+        iters = int((compare or {}).get("f64_cg_iters") or REF_ITERS_PER_TRAJ or args.ref_iters)
+        cb = cpu_sample(U0, rat_act, iters, infos[0]["n_force"])
+        cb["all_cores"] = _extra(lambda: {k: v for k, v in cpu_samples_all_cores(iters, infos[0]["n_force"])[0].items()
+                                          if k in ("value", "cores", "sample")})
+        line["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(line))
     L.close()

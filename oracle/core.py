@@ -14,24 +14,29 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
+_LIB_OMP = os.path.join(_LIBDIR, "liboracle_omp.so")
 _SRC = os.path.join(_HERE, "stag_oracle.c")
 
 MAXDEG = 32
 
 
-def build(force=False):
-    """Compile the oracle with gcc (portable flags: same results on x86 and Arm)."""
+def build(force=False, openmp=False):
+    """Compile the oracle with gcc (portable flags: same results on x86 and Arm).
+    openmp=True builds the all-cores variant (OpenMP over the site loops, same
+    arithmetic) used only to time the oracle on every host core."""
     os.makedirs(_LIBDIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
-                                              os.path.getmtime(os.path.join(_HERE, "stag_oracle.h")))):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-o", tmp, _SRC, "-lm"]
+    out = _LIB_OMP if openmp else _LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max(os.path.getmtime(_SRC),
+                                             os.path.getmtime(os.path.join(_HERE, "stag_oracle.h")))):
+        return out
+    tmp = out + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O3", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off"]
+    cmd += ["-fopenmp"] if openmp else []
+    cmd += ["-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, out)
+    return out
 
 
 class Rational(C.Structure):
@@ -71,9 +76,11 @@ _u32p = C.POINTER(C.c_uint32)
 
 
 def lib():
+    """The oracle library; the all-cores build when ORACLE_OPENMP=1 is set
+    before the first call (threads from OMP_NUM_THREADS)."""
     global _lib
     if _lib is None:
-        _lib = C.CDLL(build())
+        _lib = C.CDLL(build(openmp=os.environ.get("ORACLE_OPENMP") == "1"))
         L = _lib
         L.or_volume.restype = C.c_long
         for name in ("or_plaquette", "or_gauge_action", "or_fermion_action", "or_kinetic",

@@ -10,6 +10,12 @@
  * the test suite, the smoke check and the benchmark's CPU-baseline leg may
  * load this library.
  *
+ * The loops over sites and links that write one output per site carry
+ * OpenMP pragmas; the default build ignores them (single thread).  The
+ * all-cores build (-fopenmp) spreads only those loops over the host cores:
+ * every output is computed by the same operations in the same order, and the
+ * dot products stay serial, so both builds give identical results.
+ *
  * Layout conventions are listed in stag_oracle.h.
  */
 #include "stag_oracle.h"
@@ -320,6 +326,7 @@ void or_dslash_full(const int dims[4], const double *U, const double *in, double
     lat_init(&l, dims);
     const cplx *vin = (const cplx *)in;
     cplx *vout = (cplx *)out;
+#pragma omp parallel for schedule(static)
     for (long lex = 0; lex < l.V; lex++) hop_site(&l, U, lex, vin, 1, vout + 3 * lex);
 }
 
@@ -331,6 +338,7 @@ void or_dslash(const int dims[4], const double *U, int out_parity, const double 
     lat_init(&l, dims);
     const cplx *vin = (const cplx *)in;
     cplx *vout = (cplx *)out;
+#pragma omp parallel for schedule(static)
     for (long lex = 0; lex < l.V; lex++) {
         int x[4];
         coords(&l, lex, x);
@@ -348,6 +356,7 @@ void or_apply_M(const int dims[4], const double *U, double mass, const double *i
     double *tmp2 = malloc(sizeof(double) * 6 * Vh);
     or_dslash(dims, U, 1, in, tmp);
     or_dslash(dims, U, 0, tmp, tmp2);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < 6 * Vh; i++) out[i] = mass * mass * in[i] - tmp2[i];
     free(tmp);
     free(tmp2);
@@ -445,6 +454,7 @@ int or_multishift(const int dims[4], const double *U, double mass, int n, const 
             zeta_new[k] = zeta[k] * zeta_old[k] * alpha_old / den;
             double ak = alpha * zeta_new[k] / zeta[k];
             double *xk = x + k * N, *pkk = pk + k * N;
+#pragma omp parallel for schedule(static)
             for (long i = 0; i < N; i++) xk[i] += ak * pkk[i];
         }
         for (long i = 0; i < N; i++) r[i] -= alpha * w[i];
@@ -457,6 +467,7 @@ int or_multishift(const int dims[4], const double *U, double mass, int n, const 
             double ratio = zeta_new[k] / zeta[k];
             double bk = beta * ratio * ratio;
             double *pkk = pk + k * N;
+#pragma omp parallel for schedule(static)
             for (long i = 0; i < N; i++) pkk[i] = zeta_new[k] * r[i] + bk * pkk[i];
             zeta_old[k] = zeta[k];
             zeta[k] = zeta_new[k];
@@ -671,6 +682,7 @@ void or_gauge_force(const int dims[4], const double *U, double beta, double *F)
     olat l;
     lat_init(&l, dims);
     for (int mu = 0; mu < 4; mu++)
+#pragma omp parallel for schedule(static)
         for (long lex = 0; lex < l.V; lex++) {
             mat3 u = link_at(&l, U, mu, lex), A = staple_sum(&l, U, lex, mu);
             mat3 W = mmul(&u, &A);
@@ -713,6 +725,7 @@ int or_fermion_force(const int dims[4], const double *U, double mass, const or_r
     for (int k = 0; k < r->n; k++) or_dslash(dims, U, 1, X + k * N, Y + k * N);
     const cplx *Xc = (const cplx *)X, *Yc = (const cplx *)Y;
     for (int mu = 0; mu < 4; mu++)
+#pragma omp parallel for schedule(static)
         for (long lex = 0; lex < l.V; lex++) {
             int x[4];
             coords(&l, lex, x);
@@ -758,6 +771,7 @@ double or_kinetic(const int dims[4], const double *w)
 void or_update_links(const int dims[4], double *U, const double *w, double eps)
 {
     long V = or_volume(dims);
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < 4 * V; i++) {
         mat3 P = omega_to_mat(w + 8 * i);
         mat3 X = mscale(&P, eps);

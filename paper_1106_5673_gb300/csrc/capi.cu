@@ -138,6 +138,8 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->cg_host, sizeof(CGState));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->bcg_host, sizeof(BCGState));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->msm_host, sizeof(MSState) * STAG_MAXRHS);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->ms_poll, sizeof(MSState));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_poll, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         st = (e == cudaErrorMemoryAllocation) ? STAG_ERR_OOM : STAG_ERR_CUDA;
         cudaGetLastError();
@@ -164,6 +166,8 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     if (ctx->cg_host) cudaFreeHost(ctx->cg_host);
     if (ctx->bcg_host) cudaFreeHost(ctx->bcg_host);
     if (ctx->msm_host) cudaFreeHost(ctx->msm_host);
+    if (ctx->ms_poll) cudaFreeHost(ctx->ms_poll);
+    if (ctx->ev_poll) cudaEventDestroy(ctx->ev_poll);
     delete ctx;
     return STAG_OK;
 }

@@ -77,6 +77,46 @@ STAG_D void ms_scalar_update(MSState* st, double t0, double t1, double t2, doubl
         const int bad = !isfinite(rr_new) || !isfinite(beta) || !isfinite(alpha);
         if (bad) st->nonfinite = 1;
         st->stop_next = (n_active == 0 || iter >= st->maxit || bad) ? 1 : 0;
+        st->pend = 1;
+    }
+}
+
+// Coefficients of the shifted vectors' update of the last iteration, staged in
+// shared memory by every thread of a block (one per shift).
+template <typename R> struct MSCoef {
+    R ak[STAG_MAXSHIFT], bk[STAG_MAXSHIFT], z[STAG_MAXSHIFT];
+    int ux[STAG_MAXSHIFT], act[STAG_MAXSHIFT];
+};
+template <typename R> STAG_D void ms_load_coef(const MSState* st, MSCoef<R>& c) {
+    const int k = threadIdx.x, ns = st->n;
+    if (k < STAG_MAXSHIFT) {
+        const bool in = k < ns;
+        c.ak[k] = in ? (R)st->ak[k] : (R)0;
+        c.bk[k] = in ? (R)st->bk[k] : (R)0;
+        c.z[k] = in ? (R)st->zeta[k] : (R)0;
+        c.ux[k] = in ? st->upd_x[k] : 0;
+        c.act[k] = in ? st->active[k] : 0;
+    }
+}
+
+// The shifted vectors' update of one iteration at entry i (x_k += a_k p_k with
+// the old p_k, then p_k = zeta_k r + b_k p_k for the shifts still active),
+// with r the base residual after that iteration.
+template <typename V2, typename R>
+STAG_D void ms_shift_update_at(long i, long stride, int ns, const V2 rv, V2* __restrict__ pk, V2* __restrict__ xk,
+                               const MSCoef<R>& c) {
+    for (int k = 0; k < ns; k++) {
+        if (!c.ux[k]) continue;
+        V2 q = pk[k * stride + i];
+        V2 x = xk[k * stride + i];
+        x.x += c.ak[k] * q.x;
+        x.y += c.ak[k] * q.y;
+        xk[k * stride + i] = x;
+        if (c.act[k]) {
+            q.x = c.z[k] * rv.x + c.bk[k] * q.x;
+            q.y = c.z[k] * rv.y + c.bk[k] * q.y;
+            pk[k * stride + i] = q;
+        }
     }
 }
 

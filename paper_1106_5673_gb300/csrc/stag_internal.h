@@ -48,6 +48,7 @@ struct MSState {
     int stop_next;  // set by the residual update, applied by the last kernel of the iteration
     int n_active;
     int nonfinite;
+    int pend;       // 1: the shifted vectors' update of the last iteration is still to be applied
 };
 
 // Device-resident scalar state of one single-shift CG with reliable updates.
@@ -88,6 +89,8 @@ struct stag_ctx {
     double* hscal;      // pinned host mirror of dscal
     MSState* ms;        // device multi-shift state
     MSState* ms_host;   // pinned host mirror
+    MSState* ms_poll;   // pinned copy read one chunk behind (pipelined polling)
+    cudaEvent_t ev_poll;  // marks the arrival of ms_poll
     CGState* cg;        // device single-shift state
     CGState* cg_host;   // pinned host mirror
     BCGState* bcg;      // device batched-refinement state

@@ -139,3 +139,34 @@ def test_multishift_one_step_closed_form():
     assert tot == 1
     for k, s in enumerate(shifts):
         np.testing.assert_allclose(xs[k], b / (lam[0] + s), atol=1e-13)
+
+
+def test_all_cores_build_gives_identical_results(rationals):
+    """The OpenMP build of the oracle (used only to time it on every host
+    core) computes the same numbers bit for bit: only loops that write one
+    output per site run in parallel, and the dot products stay serial."""
+    import hashlib
+    import os
+    import subprocess
+    import sys
+    code = (
+        "import hashlib, json, sys, numpy as np\n"
+        "sys.path.insert(0, %r)\n"
+        "import oracle as O\n"
+        "from paper_1106_5673_gb300 import synth\n"
+        "r = json.load(open(%r))['p-1/2_d6_1e-2']\n"
+        "dims = (4, 4, 4, 6)\n"
+        "U = synth.near_unit_links(dims, 0.3, 3)\n"
+        "phi = synth.gaussian_vector(dims, 4)\n"
+        "F, _, _ = O.fermion_force(dims, U, 0.2, r['a0'], r['a'], r['b'], phi, tol=1e-11)\n"
+        "G = O.gauge_force(dims, U, 5.3)\n"
+        "W = O.update_links(dims, U, G, 0.01)\n"
+        "print(hashlib.sha256(F.tobytes() + G.tobytes() + W.tobytes()).hexdigest())\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+         os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rationals.json"))
+    out = {}
+    for omp in ("0", "1"):
+        env = dict(os.environ, ORACLE_OPENMP=omp, OMP_NUM_THREADS="4")
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+        out[omp] = r.stdout.strip()
+    assert len(out["0"]) == 64 and out["0"] == out["1"]
