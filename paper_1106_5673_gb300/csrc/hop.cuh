@@ -216,7 +216,10 @@ STAG_D Vec3<double> hop2_ff(const Geom& g, const float4* __restrict__ Uhi, const
     return r;
 }
 
-// 2 (D psi)(n) for the site s = (h, par); psi lives on parity 1-par.
+// 2 (D psi)(n) for the site s = (h, par); psi lives on parity 1-par.  The
+// signs (staggered phase, antiperiodic boundary) multiply the neighbour
+// vectors, so the two products of each direction are plain fused
+// multiply-add chains into one accumulator, without branches.
 template <typename R, int LP>
 STAG_D Vec3<R> hop2(const Geom& g, const void* __restrict__ U, const typename VT<R>::T* __restrict__ in,
                     int h, int par, const Site& s) {
@@ -231,11 +234,9 @@ STAG_D Vec3<R> hop2(const Geom& g, const void* __restrict__ U, const typename VT
             if (s.x[3] == 0) sb = -sb;
         }
         const Mat3<R> uf = get_link<R, LP>(U, g, mu, par, h);
-        const Vec3<R> vf = load_vec(in, fl >> 1);
-        axpy_sign(acc, sf, mv(uf, vf));
+        mv_acc(acc, uf, vsign((R)sf, load_vec(in, fl >> 1)));
         const Mat3<R> ub = get_link<R, LP>(U, g, mu, 1 - par, bl >> 1);
-        const Vec3<R> vb = load_vec(in, bl >> 1);
-        axpy_sign(acc, -sb, mdv(ub, vb));
+        mdv_acc(acc, ub, vsign((R)(-sb), load_vec(in, bl >> 1)));
     }
     return acc;
 }
@@ -267,14 +268,17 @@ STAG_D void hop2_multiR(const Geom& g, const void* __restrict__ U, const typenam
             if (s.x[3] == g.L[3] - 1) sf = -sf;
             if (s.x[3] == 0) sb = -sb;
         }
-        const Mat3<R> uf = get_link<R, LP>(U, g, mu, par, h);
+        // the sign multiplies the link once for all right-hand sides
+        Mat3<R> uf = get_link<R, LP>(U, g, mu, par, h);
+        msign((R)sf, uf);
 #pragma unroll
         for (int q = 0; q < NR; q++)
-            if (q < nj) axpy_sign(acc[q], sf, mv(uf, load_vec(in + js[q] * stride, fl >> 1)));
-        const Mat3<R> ub = get_link<R, LP>(U, g, mu, 1 - par, bl >> 1);
+            if (q < nj) mv_acc(acc[q], uf, load_vec(in + js[q] * stride, fl >> 1));
+        Mat3<R> ub = get_link<R, LP>(U, g, mu, 1 - par, bl >> 1);
+        msign((R)(-sb), ub);
 #pragma unroll
         for (int q = 0; q < NR; q++)
-            if (q < nj) axpy_sign(acc[q], -sb, mdv(ub, load_vec(in + js[q] * stride, bl >> 1)));
+            if (q < nj) mdv_acc(acc[q], ub, load_vec(in + js[q] * stride, bl >> 1));
     }
 }
 

@@ -54,11 +54,24 @@ template <typename R> STAG_HD Vec3<R> vzero() {
     return v;
 }
 
-// rebuild row 2 = conj(row0 x row1) (SU(3), det = 1)
+// rebuild row 2 = conj(row0 x row1) (SU(3), det = 1): entry c is
+// conj(a b - x y) with a = u0[c+1], b = u1[c+2], x = u0[c+2], y = u1[c+1]
+// (indices mod 3), each real part one multiply and three fused multiply-adds
 template <typename R> STAG_HD void recon_row2(Mat3<R>& u) {
-    u.e[2][0] = conj(u.e[0][1] * u.e[1][2] - u.e[0][2] * u.e[1][1]);
-    u.e[2][1] = conj(u.e[0][2] * u.e[1][0] - u.e[0][0] * u.e[1][2]);
-    u.e[2][2] = conj(u.e[0][0] * u.e[1][1] - u.e[0][1] * u.e[1][0]);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const int i1 = (c + 1) % 3, i2 = (c + 2) % 3;
+        const Cplx<R> a = u.e[0][i1], b = u.e[1][i2], x = u.e[0][i2], y = u.e[1][i1];
+        R re = a.re * b.re;
+        re = fma(-a.im, b.im, re);
+        re = fma(-x.re, y.re, re);
+        re = fma(x.im, y.im, re);
+        R im = -(a.re * b.im);
+        im = fma(-a.im, b.re, im);
+        im = fma(x.re, y.im, im);
+        im = fma(x.im, y.re, im);
+        u.e[2][c] = cmk(re, im);
+    }
 }
 
 template <typename R> STAG_HD Mat3<R> mmul(const Mat3<R>& a, const Mat3<R>& b) {
@@ -326,6 +339,51 @@ STAG_D void st_vec(float2* v, int h, const Vec3<float>& r) {
     p[2] = make_float2(r.c[2].re, r.c[2].im);
 }
 
+// acc += U v and acc += U^dag v as chains of fused multiply-adds (four per
+// complex product, the accumulation folded in)
+template <typename R> STAG_D void mv_acc(Vec3<R>& acc, const Mat3<R>& u, const Vec3<R>& v) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        R re = acc.c[a].re, im = acc.c[a].im;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            re = fma(u.e[a][c].re, v.c[c].re, re);
+            re = fma(-u.e[a][c].im, v.c[c].im, re);
+            im = fma(u.e[a][c].re, v.c[c].im, im);
+            im = fma(u.e[a][c].im, v.c[c].re, im);
+        }
+        acc.c[a] = cmk(re, im);
+    }
+}
+template <typename R> STAG_D void mdv_acc(Vec3<R>& acc, const Mat3<R>& u, const Vec3<R>& v) {
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        R re = acc.c[a].re, im = acc.c[a].im;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            re = fma(u.e[c][a].re, v.c[c].re, re);
+            re = fma(u.e[c][a].im, v.c[c].im, re);
+            im = fma(u.e[c][a].re, v.c[c].im, im);
+            im = fma(-u.e[c][a].im, v.c[c].re, im);
+        }
+        acc.c[a] = cmk(re, im);
+    }
+}
+// s v for a sign s = +-1 (exact)
+template <typename R> STAG_D Vec3<R> vsign(R s, const Vec3<R>& v) {
+    Vec3<R> r;
+#pragma unroll
+    for (int a = 0; a < 3; a++) r.c[a] = cmk(s * v.c[a].re, s * v.c[a].im);
+    return r;
+}
+// s U (all three rows) for a sign s = +-1
+template <typename R> STAG_D void msign(R s, Mat3<R>& u) {
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) u.e[a][b] = cmk(s * u.e[a][b].re, s * u.e[a][b].im);
+}
+
 // U psi and U^dag psi
 template <typename R> STAG_D Vec3<R> mv(const Mat3<R>& u, const Vec3<R>& v) {
     Vec3<R> r;
@@ -391,27 +449,48 @@ STAG_D float warp_sum_f(float v) {
     return v;
 }
 
-// Block sums of N <= 32 per-thread values of type T: returns the sum of
-// series j in lane j of warp 0 (j < N; other threads get 0).  The warp level
-// runs in T (for FP32 data: FP32 shuffles, since GB300 executes FP64 at a
-// small fraction of its FP32 rate), the cross-warp level in FP64, one lane per
-// series adding the warps' partials in order.
-template <int N, typename T> STAG_D double block_sum_nv(const T v[N]) {
-    static_assert(N <= 32, "one lane per series");
-    __shared__ double red_v[32][N];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Warp sums of N series (N a power of two <= 32) by a transposing
+// butterfly: at the exchange with lane^o (o = 16, 8, ...) each lane keeps
+// half of its series (the upper half where its bit o is set) and adds its
+// partner's copy of that half, so the series count halves at every step;
+// once one series is left, plain butterfly steps finish the sum.  N - 1 +
+// 5 - log2(N) shuffles instead of 5 N.  On return, lane l holds the warp sum
+// of series l >> (5 - log2(N)).
+template <int N, typename T> STAG_D T warp_transpose_sum(const T v[N]) {
+    static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "N a power of two <= 32");
+    const int lane = threadIdx.x & 31;
     T s[N];
 #pragma unroll
     for (int j = 0; j < N; j++) s[j] = v[j];
 #pragma unroll
-    for (int j = 0; j < N; j++) {
-        if constexpr (sizeof(T) == 4) s[j] = warp_sum_f(s[j]);
-        else s[j] = warp_sum(s[j]);
-    }
-    __syncthreads();
-    if (lane == 0)
+    for (int half = N / 2, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
 #pragma unroll
-        for (int j = 0; j < N; j++) red_v[w][j] = (double)s[j];
+        for (int i = 0; i < half; i++) {
+            const T send = up ? s[i] : s[i + half];
+            const T keep = up ? s[i + half] : s[i];
+            s[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    T r = s[0];
+#pragma unroll
+    for (int o = 16 / N; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+// Block sums of N <= 32 per-thread values of type T (N a power of two):
+// returns the sum of series j in lane j of warp 0 (j < N; other threads get
+// 0).  The warp level runs in T (for FP32 data: FP32 shuffles, since GB300
+// executes FP64 at a small fraction of its FP32 rate), the cross-warp level
+// in FP64, one lane per series adding the warps' partials in order.
+template <int N, typename T> STAG_D double block_sum_nv(const T v[N]) {
+    static_assert(N <= 32, "one lane per series");
+    __shared__ double red_v[32][N];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    constexpr int SHIFT = (N >= 32) ? 0 : (N >= 16) ? 1 : (N >= 8) ? 2 : (N >= 4) ? 3 : (N >= 2) ? 4 : 5;
+    const T ws = warp_transpose_sum<N, T>(v);
+    __syncthreads();
+    if ((lane & ((1 << SHIFT) - 1)) == 0) red_v[w][lane >> SHIFT] = (double)ws;
     __syncthreads();
     double out = 0.0;
     if (threadIdx.x < N) {
