@@ -87,11 +87,8 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
     if (V > (1L << 29)) return STAG_ERR_ARG;
     stag_ctx* ctx = new stag_ctx();
     memset(ctx->err, 0, sizeof ctx->err);
-    for (int m = 0; m < 4; m++) ctx->g.L[m] = dims[m];
+    geom_init(ctx->g, dims);
     ctx->use_graphs = 1;
-    ctx->g.V = (int)V;
-    ctx->g.Vh = (int)(V / 2);
-    ctx->g.Lx2 = dims[0] / 2;
     for (int i = 0; i < WS_NSLOTS; i++) {
         ctx->ws[i] = nullptr;
         ctx->ws_bytes[i] = 0;

@@ -21,7 +21,30 @@ struct Geom {
     int L[4];
     int V, Vh;
     int Lx2;  // Lx/2, the x-extent in half-site units
+    // n / L[m] = high 64 bits of n * mag[m], mag[m] = floor((2^64 - 1) / L[m]) + 1:
+    // exact for 0 <= n < 2^64 / L[m] (for L[m] a power of two mag = 2^64 / L;
+    // otherwise mag overestimates 2^64 / L by less than one, an error
+    // n / 2^64 < 1 / L that cannot carry the quotient past an integer)
+    unsigned long long mag[3];
 };
+
+// fills the geometry of a lattice with extents dims (each even, V < 2^29)
+STAG_HD void geom_init(Geom& g, const int dims[4]) {
+    long long V = 1;
+    for (int m = 0; m < 4; m++) {
+        g.L[m] = dims[m];
+        V *= dims[m];
+    }
+    g.V = (int)V;
+    g.Vh = (int)(V / 2);
+    g.Lx2 = dims[0] / 2;
+    for (int m = 0; m < 3; m++) g.mag[m] = (~0ull) / (unsigned long long)dims[m] + 1ull;
+}
+
+// n / L[m] for 0 <= n < 2^31
+STAG_D int gdiv(const Geom& g, int m, int n) {
+    return (int)__umul64hi((unsigned long long)(unsigned)n, g.mag[m]);
+}
 
 // ---------------------------------------------------------------- complex
 
@@ -181,12 +204,12 @@ struct Site {
 STAG_D Site site_of(const Geom& g, int h, int par) {
     Site s;
     int lex0 = 2 * h;
-    int x0 = lex0 % g.L[0];
-    int r = lex0 / g.L[0];
-    s.x[1] = r % g.L[1];
-    r /= g.L[1];
-    s.x[2] = r % g.L[2];
-    s.x[3] = r / g.L[2];
+    int r = gdiv(g, 0, lex0);
+    int x0 = lex0 - r * g.L[0];
+    int r2 = gdiv(g, 1, r);
+    s.x[1] = r - r2 * g.L[1];
+    s.x[3] = gdiv(g, 2, r2);
+    s.x[2] = r2 - s.x[3] * g.L[2];
     int p0 = (x0 + s.x[1] + s.x[2] + s.x[3]) & 1;
     s.x[0] = x0 + (p0 != par);
     s.lex = lex0 + (p0 != par);
@@ -591,12 +614,12 @@ STAG_D bool grid_reduce_series(const double* partials, double* gpart, unsigned i
 STAG_D Site site_from_lex(const Geom& g, int lex) {
     Site s;
     s.lex = lex;
-    s.x[0] = lex % g.L[0];
-    int r = lex / g.L[0];
-    s.x[1] = r % g.L[1];
-    r /= g.L[1];
-    s.x[2] = r % g.L[2];
-    s.x[3] = r / g.L[2];
+    int r = gdiv(g, 0, lex);
+    s.x[0] = lex - r * g.L[0];
+    int r2 = gdiv(g, 1, r);
+    s.x[1] = r - r2 * g.L[1];
+    s.x[3] = gdiv(g, 2, r2);
+    s.x[2] = r2 - s.x[3] * g.L[2];
     return s;
 }
 STAG_D int par_of(const Site& s) { return (s.x[0] + s.x[1] + s.x[2] + s.x[3]) & 1; }

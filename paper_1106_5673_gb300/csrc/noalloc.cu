@@ -100,10 +100,7 @@ extern "C" int stag_apply_M_noalloc(const int dims[4], const double* links, doub
         g_scratch_addr[dev] = (double2*)p;
     }
     Geom g;
-    for (int m = 0; m < 4; m++) g.L[m] = dims[m];
-    g.V = (int)V;
-    g.Vh = (int)(V / 2);
-    g.Lx2 = dims[0] / 2;
+    geom_init(g, dims);
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = (g.Vh + 127) / 128;
     double2* tmp = g_scratch_addr[dev];

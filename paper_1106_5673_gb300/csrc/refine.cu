@@ -310,22 +310,30 @@ __global__ void k_b_CD(long n, size_t stride, float2* __restrict__ R, const floa
         const int k = st->uact[a];
         const float alpha = (float)st->alpha[k], beta = (float)st->beta[k];
         const bool upd_p = !st->want_rel[k];
-        float2* r = R + k * stride;
-        const float2* w = W + k * stride;
-        float2* p = P + k * stride;
-        float2* x = XL + k * stride;
-        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
-            float2 rv = r[i], pv = p[i], xv = x[i];
-            const float2 wv = w[i];
-            rv.x -= alpha * wv.x;
-            rv.y -= alpha * wv.y;
-            xv.x += alpha * pv.x;
-            xv.y += alpha * pv.y;
+        // float4: two complex entries per access (3 Vh is even, vectors 16-byte aligned)
+        float4* r = (float4*)(R + k * stride);
+        const float4* w = (const float4*)(W + k * stride);
+        float4* p = (float4*)(P + k * stride);
+        float4* x = (float4*)(XL + k * stride);
+        const long n4 = n / 2;
+        for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+            float4 rv = r[i], pv = p[i], xv = x[i];
+            const float4 wv = w[i];
+            rv.x = fmaf(-alpha, wv.x, rv.x);
+            rv.y = fmaf(-alpha, wv.y, rv.y);
+            rv.z = fmaf(-alpha, wv.z, rv.z);
+            rv.w = fmaf(-alpha, wv.w, rv.w);
+            xv.x = fmaf(alpha, pv.x, xv.x);
+            xv.y = fmaf(alpha, pv.y, xv.y);
+            xv.z = fmaf(alpha, pv.z, xv.z);
+            xv.w = fmaf(alpha, pv.w, xv.w);
             r[i] = rv;
             x[i] = xv;
             if (upd_p) {
-                pv.x = rv.x + beta * pv.x;
-                pv.y = rv.y + beta * pv.y;
+                pv.x = fmaf(beta, pv.x, rv.x);
+                pv.y = fmaf(beta, pv.y, rv.y);
+                pv.z = fmaf(beta, pv.z, rv.z);
+                pv.w = fmaf(beta, pv.w, rv.w);
                 p[i] = pv;
             }
         }

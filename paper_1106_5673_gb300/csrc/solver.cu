@@ -265,6 +265,59 @@ __global__ void k_ms_CD(long n, long stride, V2* __restrict__ r, const V2* __res
     ms_vector_update<V2, R>(n, stride, blockIdx.x * (long)blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x, r,
                             w, p, pk, xk, st);
 }
+// FP32 vectors: the same update on float4 (two complex entries per access;
+// 3 Vh is even, so n4 = 3 Vh / 2 and every vector starts 16-byte aligned)
+template <>
+__global__ void k_ms_CD<float2, float>(long n, long stride, float2* __restrict__ r2, const float2* __restrict__ w2,
+                                       float2* __restrict__ p2, float2* __restrict__ pk2, float2* __restrict__ xk2,
+                                       MSState* st, unsigned int* counter) {
+    if (!st->live) return;
+    __shared__ MSCoef<float> c;
+    ms_load_coef<float>(st, c);
+    __syncthreads();
+    const float alpha = (float)st->alpha, beta = (float)st->beta;
+    const int ns = st->n;
+    const long n4 = n / 2, s4 = stride / 2;
+    float4* r = (float4*)r2;
+    const float4* w = (const float4*)w2;
+    float4* p = (float4*)p2;
+    float4* pk = (float4*)pk2;
+    float4* xk = (float4*)xk2;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+        float4 rv = r[i];
+        const float4 wv = w[i];
+        rv.x = fmaf(-alpha, wv.x, rv.x);
+        rv.y = fmaf(-alpha, wv.y, rv.y);
+        rv.z = fmaf(-alpha, wv.z, rv.z);
+        rv.w = fmaf(-alpha, wv.w, rv.w);
+        r[i] = rv;
+        float4 pv = p[i];
+        pv.x = fmaf(beta, pv.x, rv.x);
+        pv.y = fmaf(beta, pv.y, rv.y);
+        pv.z = fmaf(beta, pv.z, rv.z);
+        pv.w = fmaf(beta, pv.w, rv.w);
+        p[i] = pv;
+        for (int k = 0; k < ns; k++) {
+            if (!c.ux[k]) continue;
+            float4 q = pk[k * s4 + i];
+            float4 x = xk[k * s4 + i];
+            const float a = c.ak[k];
+            x.x = fmaf(a, q.x, x.x);
+            x.y = fmaf(a, q.y, x.y);
+            x.z = fmaf(a, q.z, x.z);
+            x.w = fmaf(a, q.w, x.w);
+            xk[k * s4 + i] = x;
+            if (c.act[k]) {
+                const float z = c.z[k], b = c.bk[k];
+                q.x = fmaf(b, q.x, z * rv.x);
+                q.y = fmaf(b, q.y, z * rv.y);
+                q.z = fmaf(b, q.z, z * rv.z);
+                q.w = fmaf(b, q.w, z * rv.w);
+                pk[k * s4 + i] = q;
+            }
+        }
+    }
+}
 
 template <typename V2, typename R>
 __global__ void k_ms_C(long n, V2* __restrict__ r, const V2* __restrict__ w, MSState* st, double* partials,
