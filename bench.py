@@ -156,34 +156,62 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-def hop_roofline(stag, torch, dims, nrep=30):
-    """Average duration of the FP32 D_oe hop (12-real FP32 links), each launch
-    timed with CUDA events on the launching stream after an L2 flush.
-    Algorithmic bytes per output site: 8 links x 48 B + 8 neighbours x 24 B
-    + 1 output x 24 B = 600 B."""
+# algorithmic bytes per output site of one hop, by link storage: 8 links + 8
+# neighbour vectors + 1 output vector
+HOP_BYTES = {"f32": 8 * 48 + 9 * 24,       # 12-real FP32 links, FP32 vectors: 600
+             "f32r8": 8 * 32 + 9 * 24,     # 8-real FP32 links: 472
+             "bf16": 8 * 24 + 9 * 24,      # 12-real BF16 links: 408
+             "f64": 8 * 96 + 9 * 48,       # 12-real FP64 links, FP64 vectors: 1200
+             "f64ff": 8 * 96 + 9 * 48}     # FP32 hi + lo link words (float-float): 1200
+
+
+def hop_roofline(stag, torch, dims, nrep=30, fmt="f32", L=None):
+    """Average duration of the D_oe hop with the given link storage, each
+    launch timed with CUDA events on the launching stream after an L2 flush
+    (a write of 512 MB).  Algorithmic bytes per output site: HOP_BYTES."""
     from paper_1106_5673_gb300 import synth
-    L = stag.Lattice(dims)
-    L.load_gauge(synth.near_unit_links(dims, 0.3, 5))
-    x = torch.from_numpy(synth.gaussian_vector(dims, 6)).cuda().to(torch.complex64)
-    y = L.vector(stag.PREC_F32)
+    prec = {"f32": stag.PREC_F32, "f32r8": stag.PREC_F32R8, "bf16": stag.PREC_BF16, "f64": stag.PREC_F64,
+            "f64ff": stag.PREC_F64FF}[fmt]
+    own = L is None
+    if own:
+        L = stag.Lattice(dims)
+        L.load_gauge(synth.near_unit_links(dims, 0.3, 5))
+    dt = torch.complex128 if fmt in ("f64", "f64ff") else torch.complex64
+    x = torch.from_numpy(synth.gaussian_vector(dims, 6)).cuda().to(dt)
+    y = torch.empty_like(x)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(3):
-        L.apply_doe(x, y, stag.PREC_F32)
+        L.apply_doe(x, y, prec)
     times = []
     for _ in range(nrep):
         flush.fill_(1.0)
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record()
-        L.apply_doe(x, y, stag.PREC_F32)
+        L.apply_doe(x, y, prec)
         b.record()
         b.synchronize()
         times.append(a.elapsed_time(b) * 1e-3)
-    L.close()
+    if own:
+        L.close()
     t = statistics.mean(times)
     Vh = int(np.prod(dims)) // 2
-    return {"seconds": t, "bytes": 600.0 * Vh, "gbs": 600.0 * Vh / t / 1e9,
-            "gflops": 570.0 * Vh / t / 1e9, "dims": list(dims)}
+    nb = float(HOP_BYTES[fmt])
+    return {"seconds": t, "bytes": nb * Vh, "gbs": nb * Vh / t / 1e9,
+            "gflops": 570.0 * Vh / t / 1e9, "dims": list(dims), "links": fmt, "bytes_per_site": nb}
+
+
+def link_formats(stag, torch, dims):
+    """The hop with every link storage on one lattice: 12-real FP32 against
+    8-real FP32 (Sec. 4.2's minimal parametrisation) and BF16, and the
+    FP64-accurate forms: a separate FP64 copy (FP64 arithmetic) against the
+    FP32 hi/lo word pair of Sec. 4.2 (float-float arithmetic)."""
+    from paper_1106_5673_gb300 import synth
+    L = stag.Lattice(dims)
+    L.load_gauge(synth.near_unit_links(dims, 0.3, 5))
+    out = {fmt: hop_roofline(stag, torch, dims, fmt=fmt, L=L) for fmt in ("f32", "f32r8", "bf16", "f64", "f64ff")}
+    L.close()
+    return out
 
 
 def equilibrate(stag, L, rat_hb, rat_act, seed, ntraj):
@@ -635,10 +663,10 @@ def main():
     if args.roofline_only:
         import torch
         from paper_1106_5673_gb300 import stag
-        r = hop_roofline(stag, torch, ROOF_DIMS)
+        fmts = link_formats(stag, torch, ROOF_DIMS)
         peak, kind = _peaks()
-        print(json.dumps({"roofline_only": r, "frac": r["gbs"] / peak, "peak": peak,
-                          "peak_kind": kind}))
+        print(json.dumps({"roofline_only": fmts["f32"], "frac": fmts["f32"]["gbs"] / peak, "peak": peak,
+                          "peak_kind": kind, "link_formats": fmts}))
         return 0
 
     import torch
@@ -735,9 +763,12 @@ def main():
             compare.pop("rows")
 
     roof, roof_large, batch, bsolve, learned, revers = None, None, None, None, None, None
+    formats, formats_workload = None, None
     if not args.no_extras:
         roof = hop_roofline(stag, torch, DIMS)
-        roof_large = hop_roofline(stag, torch, ROOF_DIMS)
+        formats = _extra(link_formats, stag, torch, ROOF_DIMS)
+        formats_workload = _extra(link_formats, stag, torch, DIMS)
+        roof_large = formats["f32"] if "f32" in formats else hop_roofline(stag, torch, ROOF_DIMS)
         batch = _extra(batched_hop, stag, torch)
         bsolve = _extra(batched_solve, stag, torch)
         revers = _extra(reversibility, stag, torch)
@@ -778,6 +809,15 @@ def main():
         "e2e": None if t_e2e is None else {
             "value": t_e2e, "unit": "s/trajectory", "h2d_bytes_per_step": link_bytes,
             "d2h_bytes_per_step": link_bytes, "steps": args.steps},
+        "link_formats": None if formats is None else {
+            "dims": list(ROOF_DIMS),
+            **{k: {"seconds": v["seconds"], "gbs": v["gbs"], "bytes_per_site": v["bytes_per_site"],
+                   "frac": v["gbs"] / peak}
+               for k, v in formats.items() if isinstance(v, dict) and "gbs" in v}},
+        "link_formats_workload": None if formats_workload is None else {
+            "dims": list(DIMS),
+            **{k: {"seconds": v["seconds"], "gbs": v["gbs"], "bytes_per_site": v["bytes_per_site"]}
+               for k, v in formats_workload.items() if isinstance(v, dict) and "gbs" in v}},
         "gpu_launches": launches,
         "clocks": ck,
         "equilibration": {"trajectories": args.equil, "dH": [round(d, 4) for d, _ in equil],

@@ -57,8 +57,12 @@ enum {
 /* Operator precisions.  F64FF takes and returns FP64 vectors but computes in
  * float-float arithmetic on the FP32 units (each double carried as a pair of
  * floats hi + lo, Sec. 4.2's split used for arithmetic): relative accuracy
- * ~1e-13, many times the throughput of GB300's FP64 units. */
-enum { STAG_PREC_F64 = 0, STAG_PREC_F32 = 1, STAG_PREC_BF16 = 2, STAG_PREC_F64FF = 3 };
+ * ~1e-13, many times the throughput of GB300's FP64 units.  F32R8: FP32
+ * vectors and arithmetic with 8-real links (the minimal SU(3)
+ * parametrisation Sec. 4.2 mentions: a1, a2, b0 and the phases of a0 and c0,
+ * the rest rebuilt from unitarity and det = 1; 32 bytes per link instead of
+ * 48), rebuilt from the FP64 links on first use after every change. */
+enum { STAG_PREC_F64 = 0, STAG_PREC_F32 = 1, STAG_PREC_BF16 = 2, STAG_PREC_F64FF = 3, STAG_PREC_F32R8 = 4 };
 
 /* Solver modes:
  *  F64         plain FP64 shifted CG, FP64 true-residual check of every shift;
@@ -196,8 +200,8 @@ int stag_gauge_action(stag_ctx *ctx, double beta, double *action, void *stream);
 
 /* out_even = D_eo in_odd:  (D psi)(n) = 1/2 sum_mu eta_mu(n) [U_mu(n) psi(n+mu)
  * - U_mu(n-mu)^dag psi(n-mu)].  Device vectors in the canonical layout of
- * `prec` (F64, F64FF: complex128; F32, BF16: complex64, with FP32 resp. BF16
- * links).  in and out must not alias. */
+ * `prec` (F64, F64FF: complex128; F32, BF16, F32R8: complex64, with FP32
+ * 12-real, BF16 resp. FP32 8-real links).  in and out must not alias. */
 int stag_apply_deo(stag_ctx *ctx, const void *in_odd, void *out_even, int prec, void *stream);
 /* out_odd = D_oe in_even. */
 int stag_apply_doe(stag_ctx *ctx, const void *in_even, void *out_odd, int prec, void *stream);

@@ -151,7 +151,7 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     if (!ctx) return STAG_OK;
     cudaDeviceSynchronize();
     clear_graphs(ctx);
-    void* ps[] = {ctx->U64, ctx->U32, ctx->U32lo, ctx->U16, ctx->U64_save, ctx->mom, ctx->partials,
+    void* ps[] = {ctx->U64, ctx->U32, ctx->U32lo, ctx->U16, ctx->U8, ctx->U64_save, ctx->mom, ctx->partials,
                   ctx->counter, ctx->dscal, ctx->ms, ctx->cg, ctx->bcg, ctx->msm, ctx->mm_partials,
                   ctx->gpart};
     for (void* p : ps)
@@ -316,7 +316,7 @@ int stag_apply_M(stag_ctx* ctx, double mass, const void* in_even, void* out_even
     CHECK_PTR(ctx, in_even);
     CHECK_PTR(ctx, out_even);
     if (in_even == out_even) return stag_fail(ctx, STAG_ERR_ARG, "in and out alias");
-    if (prec < 0 || prec > 3) return stag_fail(ctx, STAG_ERR_ARG, "unknown precision %d", prec);
+    if (prec < 0 || prec > STAG_PREC_F32R8) return stag_fail(ctx, STAG_ERR_ARG, "unknown precision %d", prec);
     const int dbl = (prec == STAG_PREC_F64 || prec == STAG_PREC_F64FF);
     const size_t vb = (dbl ? sizeof(double2) : sizeof(float2)) * 3 * (size_t)ctx->g.Vh;
     void* tmp = ws_get(ctx, dbl ? WS_RHI : WS_XLO, vb);

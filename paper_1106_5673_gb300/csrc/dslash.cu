@@ -72,6 +72,12 @@ static int hop_dispatch(stag_ctx* ctx, int prec, const void* in, void* out, int 
     case STAG_PREC_F64: launch_hop<double, LP64>(ctx, ctx->U64, in, out, par, scale, c, self, s); break;
     case STAG_PREC_F32: launch_hop<float, LP32>(ctx, ctx->U32, in, out, par, (float)scale, (float)c, self, s); break;
     case STAG_PREC_BF16: launch_hop<float, LP16>(ctx, ctx->U16, in, out, par, (float)scale, (float)c, self, s); break;
+    case STAG_PREC_F32R8: {
+        const float4* U8 = links_r8(ctx, s);
+        if (!U8) return STAG_ERR_OOM;
+        launch_hop<float, LP8>(ctx, U8, in, out, par, (float)scale, (float)c, self, s);
+        break;
+    }
     default: return stag_fail(ctx, STAG_ERR_ARG, "unknown precision %d", prec);
     }
     STAG_LAUNCH_CHECK(ctx, "hop");
@@ -109,7 +115,9 @@ int autotune_hops(stag_ctx* ctx, cudaStream_t s) {
     // solver kernels built on the hop, with their reductions, are more
     // sensitive to the block size than the bare hop timed here)
     const int cand[3] = {128, 64, 256};
-    for (int lp = 0; lp < 4; lp++) {
+    const float4* U8 = links_r8(ctx, s);
+    if (!U8) return STAG_ERR_OOM;
+    for (int lp = 0; lp < 5; lp++) {
         float best = 1e30f, t128 = 1e30f;
         int best_tpb = 128;
         for (int c = 0; c < 3; c++) {
@@ -119,6 +127,7 @@ int autotune_hops(stag_ctx* ctx, cudaStream_t s) {
                 case LP64: launch_hop<double, LP64>(ctx, ctx->U64, a, b, 1, 0.5, 0.0, nullptr, s, tpb); break;
                 case LP32: launch_hop<float, LP32>(ctx, ctx->U32, a, b, 1, 0.5f, 0.f, nullptr, s, tpb); break;
                 case LP16: launch_hop<float, LP16>(ctx, ctx->U16, a, b, 1, 0.5f, 0.f, nullptr, s, tpb); break;
+                case LP8: launch_hop<float, LP8>(ctx, U8, a, b, 1, 0.5f, 0.f, nullptr, s, tpb); break;
                 default:
                     k_hop_ff<<<nblocks(ctx->g.Vh, tpb), tpb, 0, s>>>(ctx->g, ctx->U32, ctx->U32lo, a, b, 1, 0.5, 0.0,
                                                                      nullptr);

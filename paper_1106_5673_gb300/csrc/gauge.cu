@@ -61,6 +61,7 @@ __global__ void k_mom_to_canonical(Geom g, const double* __restrict__ mom, doubl
 }
 
 int gauge_from_canonical(stag_ctx* ctx, const double* dev_links, cudaStream_t s) {
+    ctx->gauge_gen++;
     k_gauge_from_canonical<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, dev_links, ctx->U64, ctx->U32, ctx->U32lo,
                                                                       ctx->U16);
     STAG_LAUNCH_CHECK(ctx, "gauge_from_canonical");
@@ -323,6 +324,7 @@ __global__ void k_update_links(Geom g, double eps, const double* __restrict__ mo
 }
 
 int update_links(stag_ctx* ctx, double eps, cudaStream_t s) {
+    ctx->gauge_gen++;
     k_update_links<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, eps, ctx->mom, ctx->U64, ctx->U32, ctx->U32lo,
                                                               ctx->U16);
     STAG_LAUNCH_CHECK(ctx, "update_links");
@@ -339,9 +341,43 @@ __global__ void k_refresh_lowp(Geom g, const double2* __restrict__ U64, float4* 
 }
 
 int refresh_lowp_links(stag_ctx* ctx, cudaStream_t s) {
+    ctx->gauge_gen++;
     k_refresh_lowp<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, ctx->U64, ctx->U32, ctx->U32lo, ctx->U16);
     STAG_LAUNCH_CHECK(ctx, "refresh_lowp");
     return STAG_OK;
+}
+
+// 8-real FP32 copy of one link from the FP64 master: a1, a2, b0 rounded to
+// FP32, the phases of a0 and c0 from atan2 in FP64 (c0 from the rebuilt third
+// row)
+__global__ void k_build_r8(Geom g, const double2* __restrict__ U64, float4* U8) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * g.V) return;
+    const int h = i % g.Vh, mp = i / g.Vh;
+    const Mat3<double> u = load_link64(U64, g, mp >> 1, mp & 1, h);
+    float4* p = U8 + (size_t)mp * 2 * g.Vh + h;
+    p[0] = make_float4((float)u.e[0][1].re, (float)u.e[0][1].im, (float)u.e[0][2].re, (float)u.e[0][2].im);
+    p[g.Vh] = make_float4((float)u.e[1][0].re, (float)u.e[1][0].im, (float)atan2(u.e[0][0].im, u.e[0][0].re),
+                          (float)atan2(u.e[2][0].im, u.e[2][0].re));
+}
+
+const float4* links_r8(stag_ctx* ctx, cudaStream_t s) {
+    if (!ctx->U8) {
+        if (cudaMalloc((void**)&ctx->U8, sizeof(float4) * 16 * (size_t)ctx->g.Vh) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->U8 = nullptr;
+            stag_fail(ctx, STAG_ERR_OOM, "8-real links");
+            return nullptr;
+        }
+        ctx->u8_gen = ctx->gauge_gen - 1;
+    }
+    if (ctx->u8_gen != ctx->gauge_gen) {
+        k_build_r8<<<nblocks(4L * ctx->g.V, TPB), TPB, 0, s>>>(ctx->g, ctx->U64, ctx->U8);
+        if (stag_cuda_check(ctx, cudaGetLastError(), "build 8-real links") != STAG_OK) return nullptr;
+        ctx->nlaunch++;
+        ctx->u8_gen = ctx->gauge_gen;
+    }
+    return ctx->U8;
 }
 
 __global__ void k_axpy_mom(long n, double eps, const double* __restrict__ F, double* mom) {

@@ -12,7 +12,7 @@
 #pragma once
 #include "lattice.cuh"
 
-enum LinkPrec { LP64 = 0, LP32 = 1, LP16 = 2, LPFF = 3 };
+enum LinkPrec { LP64 = 0, LP32 = 1, LP16 = 2, LPFF = 3, LP8 = 4 };
 
 // Link arrays handed to a kernel: `u` in the kernel's link precision, `lo` the
 // FP32 low words (float-float links only).
@@ -34,6 +34,9 @@ template <> STAG_D Mat3<float> get_link<float, LP32>(const void* U, const Geom& 
 }
 template <> STAG_D Mat3<float> get_link<float, LP16>(const void* U, const Geom& g, int mu, int par, int h) {
     return load_link16((const uint2*)U, g, mu, par, h);
+}
+template <> STAG_D Mat3<float> get_link<float, LP8>(const void* U, const Geom& g, int mu, int par, int h) {
+    return load_link8((const float4*)U, g, mu, par, h);
 }
 
 template <typename R> STAG_D void axpy_sign(Vec3<R>& acc, int s, const Vec3<R>& v) {

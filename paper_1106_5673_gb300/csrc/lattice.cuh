@@ -266,6 +266,40 @@ STAG_D Mat3<float> load_link32(const float4* __restrict__ U, const Geom& g, int 
     return u;
 }
 
+// 8-real FP32 links (the minimal parametrisation of SU(3) the paper
+// mentions in Sec. 4.2 and leaves unbuilt): float4 [mu][parity][2][Vh] holding
+// (a1, a2) and (b0, arg a0, arg c0) of U = [[a0 a1 a2] [b0 b1 b2] [c0 c1 c2]].
+// The rest follows from unitarity and det U = 1 (each entry is the complex
+// conjugate of its cofactor):
+//   |a0|^2 = 1 - |a1|^2 - |a2|^2 = 1 - N,   |c0|^2 = N - |b0|^2,
+//   c1 = (b0* a2* - a1 a0* c0) / N,          c2 = -(b0* a1* + a2 a0* c0) / N,
+//   b1 = a0* c2* - a2* c0*,                  b2 = a1* c0* - a0* c1*.
+// 32 bytes per link instead of 48, for some 60 extra operations (two square
+// roots, two sine/cosine pairs, one reciprocal).
+STAG_D Mat3<float> load_link8(const float4* __restrict__ U, const Geom& g, int mu, int par, int h) {
+    const float4* p = U + (size_t)(mu * 2 + par) * 2 * g.Vh + h;
+    const float4 A = __ldg(p), B = __ldg(p + g.Vh);
+    Mat3<float> u;
+    const Cplx<float> a1 = cmk(A.x, A.y), a2 = cmk(A.z, A.w), b0 = cmk(B.x, B.y);
+    const float N = fmaf(a1.re, a1.re, fmaf(a1.im, a1.im, fmaf(a2.re, a2.re, a2.im * a2.im)));
+    const float ra0 = sqrtf(fmaxf(0.f, 1.f - N));
+    const float rc0 = sqrtf(fmaxf(0.f, N - fmaf(b0.re, b0.re, b0.im * b0.im)));
+    float s0, c0s, s2, c2s;
+    __sincosf(B.z, &s0, &c0s);
+    __sincosf(B.w, &s2, &c2s);
+    const Cplx<float> a0 = cmk(ra0 * c0s, ra0 * s0), c0 = cmk(rc0 * c2s, rc0 * s2);
+    const float inv = 1.f / N;
+    const Cplx<float> ac = conj(a0) * c0;  // a0* c0
+    const Cplx<float> c1 = inv * (conj(b0) * conj(a2) - a1 * ac);
+    const Cplx<float> c2 = -inv * (conj(b0) * conj(a1) + a2 * ac);
+    u.e[0][0] = a0; u.e[0][1] = a1; u.e[0][2] = a2;
+    u.e[1][0] = b0;
+    u.e[1][1] = conj(a0) * conj(c2) - conj(a2) * conj(c0);
+    u.e[1][2] = conj(a1) * conj(c0) - conj(a0) * conj(c1);
+    u.e[2][0] = c0; u.e[2][1] = c1; u.e[2][2] = c2;
+    return u;
+}
+
 STAG_D float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
 STAG_D float bf_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
 

@@ -50,7 +50,8 @@ static Links make_links(const stag_ctx* ctx, int lp) {
     L.lo = ctx->U32lo;
     L.u = (lp == LP64) ? (const void*)ctx->U64
           : (lp == LP32 || lp == LPFF) ? (const void*)ctx->U32
-                                       : (const void*)ctx->U16;
+          : (lp == LP8) ? (const void*)ctx->U8
+                        : (const void*)ctx->U16;
     return L;
 }
 
@@ -1312,7 +1313,14 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
     } else if (mode == STAG_SOLVE_LEARNED) {
         st = STAG_OK;  // learned_solve below runs its own solvers
     } else if (mode == STAG_SOLVE_MIXED || mode == STAG_SOLVE_MIXED_BF16) {
-        if (mode == STAG_SOLVE_MIXED)
+        // STAG_MS_LINKS8=1: the FP32 shifted CG reads 8-real links (the
+        // refinement keeps the 12-real FP32 links)
+        static int r8 = -1;
+        if (r8 < 0) r8 = env_int("STAG_MS_LINKS8", 0);
+        if (mode == STAG_SOLVE_MIXED && r8) {
+            if (!links_r8(ctx, s)) return STAG_ERR_OOM;
+            st = ms_core<float, LP8>(ctx, mass, n, shifts, src, X, ms_tol32(tol), maxit, info, s);
+        } else if (mode == STAG_SOLVE_MIXED)
             st = ms_core<float, LP32>(ctx, mass, n, shifts, src, X, ms_tol32(tol), maxit, info, s);
         else
             st = ms_core<float, LP16>(ctx, mass, n, shifts, src, X, ms_tol32(tol, LP16), maxit, info, s);

@@ -78,6 +78,9 @@ struct stag_ctx {
     float4* U32;        // [4][2][3][Vh]
     float4* U32lo;      // [4][2][3][Vh]  fl32(U64 - U32): low words of the float-float links
     uint2* U16;         // [4][2][3][Vh]
+    float4* U8;         // [4][2][2][Vh]  8-real FP32 links, built on first use (null until then)
+    long long gauge_gen;  // incremented whenever the links change
+    long long u8_gen;     // gauge_gen at the last rebuild of U8
     double2* U64_save;  // copy kept for the Metropolis reject
     double* mom;        // [4][2][8][Vh]
     int gauge_loaded;
@@ -104,7 +107,7 @@ struct stag_ctx {
     std::map<std::string, cudaGraphExec_t> graphs;
     int num_sms;
     long long nlaunch;  // kernels launched (graph nodes counted individually)
-    int tpb[4];         // tuned threads per block of the hop kernels, per link precision (0: default)
+    int tpb[5];         // tuned threads per block of the hop kernels, per link precision (0: default)
     int tuned;
     stag_net* net;      // preconditioner of STAG_SOLVE_LEARNED (borrowed)
     int use_graphs;     // 1: solver iteration chunks run as cached CUDA graphs
@@ -143,6 +146,8 @@ int kinetic_sum(stag_ctx* ctx, double* dst_dev, cudaStream_t s);           // 1/
 // F (internal layout) = coeff * gauge force (+ F if accumulate)
 int gauge_force_internal(stag_ctx* ctx, double beta, double* F, int accumulate, cudaStream_t s);
 int update_links(stag_ctx* ctx, double eps, cudaStream_t s);
+// the 8-real FP32 links, rebuilt from the FP64 master if the links changed since
+const float4* links_r8(stag_ctx* ctx, cudaStream_t s);
 int update_momenta(stag_ctx* ctx, const double* F, double eps, cudaStream_t s);
 int momenta_heatbath(stag_ctx* ctx, uint32_t seed, uint32_t traj, cudaStream_t s);
 int pf_gaussian(stag_ctx* ctx, uint32_t seed, uint32_t traj, int pf, double2* out, cudaStream_t s);

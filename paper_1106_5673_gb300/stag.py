@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libstag.so")
 
 OK, ERR_ARG, ERR_CUDA, ERR_NOCONV, ERR_NONFINITE, ERR_OOM, ERR_STATE = 0, -1, -2, -3, -4, -5, -6
-PREC_F64, PREC_F32, PREC_BF16, PREC_F64FF = 0, 1, 2, 3
+PREC_F64, PREC_F32, PREC_BF16, PREC_F64FF, PREC_F32R8 = 0, 1, 2, 3, 4
 SOLVE_F64, SOLVE_MIXED, SOLVE_MIXED_BF16, SOLVE_F64FF, SOLVE_LEARNED = 0, 1, 2, 3, 4
 INT_LEAPFROG, INT_OMELYAN = 0, 1
 MAXSHIFT = 32

@@ -75,6 +75,34 @@ def test_dslash_low_precision(S, dims, prec, tol):
 
 
 @pytest.mark.parametrize("dims", SHAPES)
+@pytest.mark.parametrize("links", ["near_unit", "haar"])
+def test_dslash_8_real_links(S, dims, links):
+    """FP32 hop with 8-real links (Sec. 4.2's minimal parametrisation): the
+    rebuilt links are SU(3) to FP32 rounding amplified by 1/N in the two
+    cofactor divisions (N = |a1|^2 + |a2|^2; a few 1e-6 for Haar links), so
+    the operator agrees with the FP64 oracle to 1e-5 relative.  After a link
+    update the 8-real copy is rebuilt (the second comparison)."""
+    U = synth.near_unit_links(dims, 0.5, 4) if links == "near_unit" else synth.haar_links(dims, 44)
+    L = S.Lattice(dims)
+    L.load_gauge(U)
+    x = synth.gaussian_vector(dims, 5)
+    for par_out, fn in ((1, L.apply_doe), (0, L.apply_deo)):
+        out = L.vector(S.PREC_F32R8)
+        fn(dev(x, torch.complex64), out, S.PREC_F32R8)
+        assert rel(host(out), O.dslash(dims, U, par_out, x)) < 1e-5
+    w = synth.gaussian_momenta(dims, 45)
+    L.load_momenta(w)
+    L.update_links(0.05)
+    U2 = L.store_gauge()
+    out = L.vector(S.PREC_F32R8)
+    L.apply_doe(dev(x, torch.complex64), out, S.PREC_F32R8)
+    assert rel(host(out), O.dslash(dims, U2, 1, x)) < 1e-5
+    y = L.vector(S.PREC_F32R8)
+    L.apply_M(0.1, dev(x, torch.complex64), y, S.PREC_F32R8)
+    assert rel(host(y), O.apply_M(dims, U2, 0.1, x)) < 1e-5
+
+
+@pytest.mark.parametrize("dims", SHAPES)
 def test_M_ee_f64_and_f32(S, dims):
     U = synth.haar_links(dims, 6)
     L = S.Lattice(dims)
