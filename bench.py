@@ -419,6 +419,81 @@ def reversibility(stag, torch, nmd=10, ngauge=2):
     return out
 
 
+# the solver settings of the paper's precision study (Sec. 4.4): (name,
+# Metropolis solver, r_metro, MD solver, r_md); "mixed" is the library's FP32
+# form (FP32 operator and gauge force; link and momentum updates stay FP64)
+PRECISION_SETTINGS = [("D1", "f64", 1e-9, "f64", 1e-9), ("D2", "f64", 1e-7, "f64", 1e-7),
+                      ("D3", "f64", 1e-5, "f64", 1e-5), ("D4", "f64", 1e-3, "f64", 1e-3),
+                      ("F1", "mixed", 1e-3, "mixed", 1e-3), ("MP1", "f64", 1e-9, "mixed", 1e-3),
+                      ("MP2", "f64", 1e-7, "mixed", 1e-3)]
+
+
+def precision_study(stag, torch, lattices=((16, 16, 16, 4),), scan=((12, 1), (12, 2), (12, 4), (12, 8), (6, 5),
+                                                                  (24, 5)), big=(32, 32, 32, 4)):
+    """The paper's precision study (Sec. 4.4): N_f = 2 (two pseudofermions,
+    degree-8 MD and degree-15 Metropolis rationals), beta = 5.264,
+    am = 0.01335, multi-step 2MN integrator, tau = 1.  From one thermalised
+    configuration, fixed momenta and pseudofermions, every solver setting
+    D1..MP2: the reversibility violations Delta C and Delta M (integrate to
+    tau, flip the momenta, integrate back) and the energy violation dH of one
+    trajectory from the same start and random numbers.  Then Delta M against
+    the number of gauge updates n_md x dtau_f/dtau_g (MP1 setting), and the
+    MP1 and D1 points on the larger lattice."""
+    from paper_1106_5673_gb300 import synth
+    beta, m = 5.264, 0.01335
+    lo, hi = m * m / 2, 64.0
+    a_md = stag.remez(-0.25, lo, hi, 8)[:3]      # x^{-1/(2 npf)}, npf = 2
+    a_metro = stag.remez(-0.25, lo, hi, 15)[:3]
+    h = stag.remez(0.125, lo, hi, 15)[:3]        # x^{+1/(4 npf)}
+    modes = {"f64": stag.SOLVE_F64, "mixed": stag.SOLVE_MIXED}
+
+    def params(md, r_md, metro, r_metro, nmd, ngauge, seed=81, traj=0):
+        return stag.make_params(beta, m, 1.0, nmd, stag.INT_OMELYAN, h, a_metro, a_md, npf=2, tol_md=r_md,
+                                tol_metro=r_metro, mode_md=modes[md], mode_metro=modes[metro], ngauge=ngauge,
+                                seed=seed, traj=traj)
+
+    def run(dims, nmd, ngauge, settings, with_dH=True):
+        L = stag.Lattice(dims)
+        L.load_gauge(synth.near_unit_links(dims, 0.3, 80))
+        thermalise(stag, L, a_md, 83, beta=beta)
+        for i in range(3):  # RHMC trajectories with Metropolis: fermions in equilibrium
+            L.md_trajectory(params("mixed", 1e-7, "mixed", 1e-10, nmd, ngauge, traj=1000 + i))
+        U0 = L.store_gauge()
+        W0 = synth.gaussian_momenta(dims, 84)
+        phis = torch.stack([L.rational_apply(m, h, L.pf_gaussian(85, 0, pf), tol=1e-12)[0] for pf in range(2)])
+        dof = 4 * 8 * int(np.prod(dims))
+        rows = {"lattice": list(dims), "n_md": nmd, "dtau_f_over_dtau_g": 2 * ngauge,
+                "gauge_updates": nmd * 2 * ngauge, "plaquette": L.plaquette()}
+        for name, metro, r_metro, md, r_md in settings:
+            p = params(md, r_md, metro, r_metro, nmd, ngauge)
+            L.load_gauge(U0)
+            L.load_momenta(W0)
+            t0 = time.perf_counter()
+            it, _ = L.md_integrate(p, phis)
+            t_md = time.perf_counter() - t0
+            L.load_momenta(-L.store_momenta())
+            L.md_integrate(p, phis)
+            dC = float(np.sqrt((np.abs(L.store_gauge() - U0) ** 2).sum() / dof))
+            dM = float(np.sqrt(((L.store_momenta() + W0) ** 2).sum() / dof))
+            row = {"delta_C": dC, "delta_M": dM, "cg_iters_md": it, "seconds_md": t_md}
+            if with_dH:
+                L.load_gauge(U0)
+                info = L.md_trajectory(params(md, r_md, metro, r_metro, nmd, ngauge, traj=7))
+                row["dH"] = info["dH"]
+            rows[name] = row
+        L.close()
+        return rows
+
+    out = {"beta": beta, "mass": m, "npf": 2, "md_degree": 8, "metro_degree": 15, "integrator": "2MN multi-step",
+           "settings": {n: {"metro": (me, rm), "md": (md, rd)} for n, me, rm, md, rd in PRECISION_SETTINGS}}
+    out["runs"] = [run(d, 12, 5, PRECISION_SETTINGS) for d in lattices]
+    mp1 = [s_ for s_ in PRECISION_SETTINGS if s_[0] == "MP1"]
+    out["gauge_update_scan"] = [run(lattices[0], nmd, ng, mp1, with_dH=False) for nmd, ng in scan]
+    if big:
+        out["large"] = run(big, 16, 8, [s_ for s_ in PRECISION_SETTINGS if s_[0] in ("D1", "MP1")])
+    return out
+
+
 def learned_preconditioner(stag, torch, L, shift, npairs=16, epochs=60):
     """The gauge-covariant network preconditioner on the workload's own
     lattice and lightest pole.  Two kinds of (source, solution) pairs:
@@ -640,6 +715,8 @@ def main():
                          "float-float and timed forms (dH, accept and time per form)")
     ap.add_argument("--no-ktable", action="store_true",
                     help="skip the CUPTI kernel table of one extra trajectory")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="only run the paper's precision study (Sec. 4.4) and print it as JSON")
     args = ap.parse_args()
     ROOF_DIMS = tuple(int(x) for x in args.roof_dims.split(","))
     if args.impl == "reference":
@@ -659,6 +736,11 @@ def main():
         print(json.dumps({"solve_only": {"seconds": time.perf_counter() - t0, "iters": info.iters,
                                          "refine_iters": list(info.refine_iters[:len(b)]),
                                          "max_true_resid": max(info.true_resid[:len(b)])}}))
+        return 0
+    if args.precision_study:
+        import torch
+        from paper_1106_5673_gb300 import stag
+        print(json.dumps({"precision_study": precision_study(stag, torch)}))
         return 0
     if args.roofline_only:
         import torch
