@@ -380,6 +380,35 @@ def batched_solve(stag, torch):
             "multishift_iters": iters, "max_true_resid": maxres}
 
 
+def c2_solves(stag, torch, dims=(16, 16, 16, 4), nrep=3):
+    """The 16^3x4 solver workload: Haar links (seeded), m = 0.05, 16
+    log-spaced shifts in [1e-4, 1] added to M_ee, complex Gaussian source on
+    even sites; the FP32 multi-shift with FP64-accurate refinement against
+    the FP64 shifted CG (and the float-float form), every shift to 1e-10 in
+    its FP64-accurate true residual.  Seconds per solve (best of nrep after a
+    warm-up) and iterations."""
+    from paper_1106_5673_gb300 import synth
+    L = stag.Lattice(dims)
+    L.load_gauge(synth.haar_links(dims, 31))
+    b = torch.from_numpy(synth.gaussian_vector(dims, 32)).cuda()
+    shifts = synth.log_shifts(16, 1e-4, 1.0)
+    out = {"lattice": list(dims), "mass": 0.05, "shifts": 16, "tol": 1e-10}
+    for name, mode in (("mixed", stag.SOLVE_MIXED), ("f64", stag.SOLVE_F64), ("ff", stag.SOLVE_F64FF)):
+        L.multishift_solve(0.05, shifts, b, tol=1e-10, mode=mode)
+        best = None
+        for _ in range(nrep):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = L.multishift_solve(0.05, shifts, b, tol=1e-10, mode=mode)
+            torch.cuda.synchronize()
+            t = time.perf_counter() - t0
+            best = t if best is None else min(best, t)
+        out[name] = {"seconds": best, "iters": info.iters, "refine_iters": sum(info.refine_iters[:16]),
+                     "max_true_resid": max(info.true_resid[:16])}
+    L.close()
+    return out
+
+
 def reversibility(stag, torch, nmd=10, ngauge=2):
     """The paper's reversibility test (Sec. 4.4) on its 4x16^3 lattice at
     beta 5.264, am 0.01335, two pseudofermions, degree-8 MD and degree-15
@@ -428,6 +457,39 @@ PRECISION_SETTINGS = [("D1", "f64", 1e-9, "f64", 1e-9), ("D2", "f64", 1e-7, "f64
                       ("MP2", "f64", 1e-7, "mixed", 1e-3)]
 
 
+def learned_c5(stag, torch, dims=(32, 32, 32, 32), beta=5.6, mass=0.005, nrhmc=2, npairs=32, epochs=40):
+    """The learned-preconditioner workload at its lattice size (32^4, beta 5.6,
+    m 0.005): links from the pure-gauge thermalisation and nrhmc mixed RHMC
+    trajectories with the Metropolis test (every solve to 1e-10); the network
+    trained on npairs solver-generated and on npairs operator pairs for the
+    lightest pole of the degree-15 x^{-1/2} rational on [1e-5, 64]; flexible
+    CG with it against plain CG, both to 1e-10."""
+    from paper_1106_5673_gb300 import synth
+    a0, a, b, _ = stag.remez(-0.5, 1e-5, 64.0, 15)
+    h = stag.remez(0.25, 1e-5, 64.0, 15)[:3]
+    L = stag.Lattice(dims)
+    L.load_gauge(synth.near_unit_links(dims, 0.3, 90))
+    t0 = time.perf_counter()
+    plaq = thermalise(stag, L, (a0, a, b), 91, beta=beta)
+    dHs = []
+    for i in range(nrhmc):
+        p = stag.make_params(beta, mass, 1.0, NSTEPS, stag.INT_OMELYAN, h, (a0, a, b), (a0, a, b),
+                             mode_md=stag.SOLVE_MIXED, mode_metro=stag.SOLVE_MIXED, seed=92, traj=i)
+        dHs.append(L.md_trajectory(p)["dH"])
+    t_ens = time.perf_counter() - t0
+    global MASS
+    saved, MASS = MASS, mass
+    try:
+        out = learned_preconditioner(stag, torch, L, min(b), npairs=npairs, epochs=epochs)
+    finally:
+        MASS = saved
+    out.update({"beta": beta, "mass": mass, "ensemble": {"pure_gauge_trajectories": THERM, "rhmc_trajectories": nrhmc,
+                                                         "dH": dHs, "plaquette": L.plaquette(), "seconds": t_ens,
+                                                         "therm_plaquette": plaq}})
+    L.close()
+    return out
+
+
 def precision_study(stag, torch, lattices=((16, 16, 16, 4),), scan=((12, 1), (12, 2), (12, 4), (12, 8), (6, 5),
                                                                   (24, 5)), big=(32, 32, 32, 4)):
     """The paper's precision study (Sec. 4.4): N_f = 2 (two pseudofermions,
@@ -460,7 +522,7 @@ def precision_study(stag, torch, lattices=((16, 16, 16, 4),), scan=((12, 1), (12
             L.md_trajectory(params("mixed", 1e-7, "mixed", 1e-10, nmd, ngauge, traj=1000 + i))
         U0 = L.store_gauge()
         W0 = synth.gaussian_momenta(dims, 84)
-        phis = torch.stack([L.rational_apply(m, h, L.pf_gaussian(85, 0, pf), tol=1e-12)[0] for pf in range(2)])
+        phis = torch.stack([L.rational_apply(m, h, L.pf_gaussian(85, 0, pf), tol=1e-10)[0] for pf in range(2)])
         dof = 4 * 8 * int(np.prod(dims))
         rows = {"lattice": list(dims), "n_md": nmd, "dtau_f_over_dtau_g": 2 * ngauge,
                 "gauge_updates": nmd * 2 * ngauge, "plaquette": L.plaquette()}
@@ -717,6 +779,8 @@ def main():
                     help="skip the CUPTI kernel table of one extra trajectory")
     ap.add_argument("--precision-study", action="store_true",
                     help="only run the paper's precision study (Sec. 4.4) and print it as JSON")
+    ap.add_argument("--learned-c5", action="store_true",
+                    help="only run the learned-preconditioner workload on 32^4 and print it as JSON")
     args = ap.parse_args()
     ROOF_DIMS = tuple(int(x) for x in args.roof_dims.split(","))
     if args.impl == "reference":
@@ -736,6 +800,11 @@ def main():
         print(json.dumps({"solve_only": {"seconds": time.perf_counter() - t0, "iters": info.iters,
                                          "refine_iters": list(info.refine_iters[:len(b)]),
                                          "max_true_resid": max(info.true_resid[:len(b)])}}))
+        return 0
+    if args.learned_c5:
+        import torch
+        from paper_1106_5673_gb300 import stag
+        print(json.dumps({"learned_c5": learned_c5(stag, torch)}))
         return 0
     if args.precision_study:
         import torch
@@ -845,7 +914,7 @@ def main():
             compare.pop("rows")
 
     roof, roof_large, batch, bsolve, learned, revers = None, None, None, None, None, None
-    formats, formats_workload = None, None
+    formats, formats_workload, c2 = None, None, None
     if not args.no_extras:
         roof = hop_roofline(stag, torch, DIMS)
         formats = _extra(link_formats, stag, torch, ROOF_DIMS)
@@ -853,6 +922,7 @@ def main():
         roof_large = formats["f32"] if "f32" in formats else hop_roofline(stag, torch, ROOF_DIMS)
         batch = _extra(batched_hop, stag, torch)
         bsolve = _extra(batched_solve, stag, torch)
+        c2 = _extra(c2_solves, stag, torch)
         revers = _extra(reversibility, stag, torch)
         learned = _extra(learned_preconditioner, stag, torch, L, min(rat_act[2]))
     peak, peak_kind = _peaks()
@@ -912,6 +982,7 @@ def main():
         "kernel_table": ktable,
         "batched_hop": batch,
         "batched_solve": bsolve,
+        "c2_solves": c2,
         "learned_preconditioner": learned,
         "reversibility": revers,
     }
