@@ -41,12 +41,16 @@ DIMS = (32, 32, 32, 8)
 BETA, MASS, TAU, NSTEPS, DEG, LO, HI, TOL = 5.5, 0.0075, 1.0, 20, 15, 1e-5, 64.0, 1e-10
 ROOF_DIMS = (64, 64, 64, 16)  # working set >= 4x L2 for the Dslash roofline
 THERM, THERM_STEPS = 60, 40   # pure-gauge thermalisation: trajectories, Omelyan steps (tau = 1)
+# the pure-gauge stage runs at a higher beta, whose plaquette (~0.55) is near
+# that of the dynamical-fermion ensemble at BETA; the RHMC trajectories at
+# BETA then start close to their equilibrium
+THERM_BETA = 5.7
 EQUIL = 10                    # RHMC trajectories with Metropolis after it (fermion equilibration)
-# DRAM bytes (read + write) per output site of k_hop<float,1> from one ncu
-# capture at 48^3x16: 383.8 MB / 884736 sites; traffic grows in proportion to
-# the sites, so it is scaled to the roofline lattice by Vh.  Algorithmic
-# bytes per site: 600.
-HOP_TRAFFIC_PER_SITE = 433.8
+# DRAM bytes (read + write) per output site of k_hop<float,1> on the roofline
+# lattice 64^3x16 itself, from an ncu capture of three launches
+# (dram__bytes_read.sum + dram__bytes_write.sum = 884.7 MB + 43.2 MB per
+# launch, 2097152 output sites); algorithmic bytes per site: 600
+HOP_TRAFFIC_PER_SITE = 442.5
 # total multi-shift iterations of one FP64 trajectory of this workload, as
 # counted by the library's FP64 path (identical to the oracle's recursion);
 # used to scale the oracle's per-iteration cost to a trajectory
@@ -89,8 +93,8 @@ def workload_config(therm=THERM, world=1, equil=EQUIL):
             "rational_range": [LO, HI], "tol": TOL,
             "parallelism": "replicas" if world > 1 else "single",
             "start": {"links": "exp(i 0.3 H)",
-                      "thermalisation": "%d pure-gauge MD trajectories (tau 1, %d Omelyan steps, "
-                                        "no Metropolis)" % (therm, THERM_STEPS),
+                      "thermalisation": "%d pure-gauge MD trajectories at beta %.2f (tau 1, %d Omelyan steps, "
+                                        "no Metropolis)" % (therm, THERM_BETA, THERM_STEPS),
                       "equilibration": "%d RHMC trajectories with Metropolis (MD solves 1e-7, "
                                        "Metropolis solves 1e-10)" % equil},
             "l2": "working set > L2 (links fp64+fp32+bf16 ~176 MB, solver vectors ~200 MB)"}
@@ -841,7 +845,7 @@ def main():
     L = stag.Lattice(DIMS)
     seeds = replica_seeds(rank)
     L.load_gauge(synth.near_unit_links(DIMS, 0.3, seeds["links"]))
-    plaq_therm = thermalise(stag, L, rat_act, seeds["therm"], args.therm)
+    plaq_therm = thermalise(stag, L, rat_act, seeds["therm"], args.therm, beta=THERM_BETA)
     equil = equilibrate(stag, L, rat_hb, rat_act, seeds["rng"], args.equil)
     plaq_start = L.plaquette()
     U0 = L.store_gauge()

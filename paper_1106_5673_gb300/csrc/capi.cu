@@ -59,14 +59,6 @@ void* ws_get(stag_ctx* ctx, int slot, size_t bytes) {
 static inline cudaStream_t S(void* s) { return (cudaStream_t)s; }
 static int aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-int pdl_on() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = getenv("STAG_PDL");
-        v = e ? atoi(e) : 0;
-    }
-    return v;
-}
 
 #define CHECK_CTX(ctx)                                      \
     do {                                                    \

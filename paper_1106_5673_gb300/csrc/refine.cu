@@ -45,7 +45,6 @@ STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
 template <int LP>
 __global__ void __launch_bounds__(256, 4) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
                                                  float2* __restrict__ T, size_t stride, BCGState* st) {
-    pdl_wait();
     // a stop requested by the previous iteration takes effect here, after that
     // iteration's vector update
     const int live = st->live, stop = st->stop_next;
@@ -218,7 +217,6 @@ __global__ void __launch_bounds__(256, 4) k_b_B3(Geom g, const void* __restrict_
                                                   const float2* __restrict__ P, const float2* __restrict__ R,
                                                   float2* __restrict__ W, size_t stride, BCGState* st,
                                                   double* partials, double* gpart, unsigned int* counter) {
-    pdl_wait();
     if (!st->live) return;
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     const int q0 = blockIdx.y * NR, nact = st->n_act;
@@ -306,7 +304,6 @@ __global__ void __launch_bounds__(256, 4) k_b_B3(Geom g, const void* __restrict_
 
 __global__ void k_b_CD(long n, size_t stride, float2* __restrict__ R, const float2* __restrict__ W,
                        float2* __restrict__ P, float2* __restrict__ XL, BCGState* st, unsigned int* counter) {
-    pdl_wait();
     if (!st->live) return;
     const int a = blockIdx.y;
     if (a < st->n_uact) {
@@ -439,15 +436,15 @@ void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
     for (int i = 0; i < a.chunk; i++) {
         if (a.fused) {
             if (a.lp == LP32) {
-                launch_k(k_b_A<LP32>, gh, a.tpb, cs, g, a.U.u, (const float2*)a.P, a.T, stride, ctx->bcg);
-                launch_k(k_b_B3<LP32>, gh, a.tpb, cs, g, a.U.u, (const float2*)a.T, (const float2*)a.P,
-                         (const float2*)a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart, ctx->counter);
+                k_b_A<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+                k_b_B3<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart,
+                                                     ctx->counter);
             } else {
                 k_b_A<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
                 k_b_B3<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart,
                                                      ctx->counter);
             }
-            launch_k(k_b_CD, gb, BLAS_TPB, cs, n3, stride, a.R, (const float2*)a.W, a.P, a.XL, ctx->bcg, ctx->counter);
+            k_b_CD<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, ctx->counter);
             continue;
         }
         if (a.lp == LP32) {

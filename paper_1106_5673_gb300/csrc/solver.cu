@@ -61,7 +61,6 @@ template <typename R, int LP>
 __global__ void __launch_bounds__(256) k_ms_A(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ t, MSState* st) {
-    pdl_wait();
     // the stop requested by the previous iteration's scalar update takes
     // effect here, after that iteration's vector update has run
     const int live = st->live, stop = st->stop_next;
@@ -154,7 +153,6 @@ __global__ void __launch_bounds__(256) k_ms_B3(Geom g, Links U, const typename V
                                                    const typename VT<R>::T* __restrict__ r,
                                                    typename VT<R>::T* __restrict__ w, MSState* st, double* partials,
                                                    double* gpart, unsigned int* counter) {
-    pdl_wait();
     // the previous A2 has applied any pending shifted update; the scalar
     // update of this kernel's last block sets it again (after this write: the
     // grid reduction's fence and counter order block 0 before the last block)
@@ -264,7 +262,6 @@ __global__ void k_ms_clear_pend(MSState* st) { st->pend = 0; }
 template <typename V2, typename R>
 __global__ void k_ms_CD(long n, long stride, V2* __restrict__ r, const V2* __restrict__ w, V2* __restrict__ p,
                         V2* __restrict__ pk, V2* __restrict__ xk, MSState* st, unsigned int* counter) {
-    pdl_wait();
     if (!st->live) return;
     ms_vector_update<V2, R>(n, stride, blockIdx.x * (long)blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x, r,
                             w, p, pk, xk, st);
@@ -275,7 +272,6 @@ template <>
 __global__ void k_ms_CD<float2, float>(long n, long stride, float2* __restrict__ r2, const float2* __restrict__ w2,
                                        float2* __restrict__ p2, float2* __restrict__ pk2, float2* __restrict__ xk2,
                                        MSState* st, unsigned int* counter) {
-    pdl_wait();
     if (!st->live) return;
     __shared__ MSCoef<float> c;
     ms_load_coef<float>(st, c);
@@ -701,12 +697,12 @@ void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
         k_ms_C2<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, ctx->ms);
         return;
     }
-    launch_k(k_ms_A<R, LP>, nb_hop, tpb, s, g, U, (const V2*)b.p, (V2*)b.t, ctx->ms);
+    k_ms_A<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, ctx->ms);
     if (fused_iter() == 1) {  // shifted updates in the vector kernel (A, B3, CD)
-        launch_k(k_ms_B3<R, LP>, nb_hop, tpb, s, g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
-                 ctx->ms, ctx->partials, ctx->gpart, ctx->counter);
-        launch_k(k_ms_CD<V2, R>, nb_blas, BLAS_TPB, s, n, n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, (V2*)b.pk,
-                 (V2*)b.xk, ctx->ms, ctx->counter);
+        k_ms_B3<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
+                                                 ctx->ms, ctx->partials, ctx->gpart, ctx->counter);
+        k_ms_CD<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, (V2*)b.pk,
+                                                   (V2*)b.xk, ctx->ms, ctx->counter);
         return;
     }
     k_ms_B<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (V2*)b.w, ctx->ms,

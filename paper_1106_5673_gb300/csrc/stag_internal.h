@@ -136,33 +136,6 @@ void* ws_get(stag_ctx* ctx, int slot, size_t bytes);
 
 static inline int nblocks(long n, int threads) { return (int)((n + threads - 1) / threads); }
 
-// Programmatic dependent launch (STAG_PDL=1): the solver iterations' kernels
-// are launched with programmatic stream serialisation, so that a kernel's
-// launch overlaps the end of the previous one; each such kernel starts with
-// pdl_wait(), which blocks until the previous kernel has completed and its
-// writes are visible (a no-op for kernels launched without the attribute),
-// then lets the next kernel launch.
-int pdl_on();
-STAG_D void pdl_wait() {
-#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 900)
-    cudaGridDependencySynchronize();
-    cudaTriggerProgrammaticLaunchCompletion();
-#endif
-}
-template <typename... KArgs, typename... Args>
-static inline void launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = pdl_on() ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k, args...);
-}
 
 // ---------------------------------------------------------------- gauge.cu
 int gauge_from_canonical(stag_ctx* ctx, const double* dev_links, cudaStream_t s);
