@@ -128,7 +128,7 @@ typedef struct {
     int solve_mode_metro;       /* STAG_SOLVE_* for heatbath and action solves      */
     int maxit;                  /* iteration cap of every solve                     */
     uint32_t seed, traj;        /* Philox key (seed, traj)                          */
-    int use_graphs;             /* 1: every solver iteration chunk (16 iterations
+    int use_graphs;             /* 1: every solver iteration chunk (32 iterations
                                    of a shifted or batched CG) runs as a cached
                                    CUDA graph, replayed between the host's
                                    convergence polls; 0: the same kernels are

@@ -268,7 +268,7 @@ int multishift_solve_multi(stag_ctx* ctx, double mass, int nsys, int n, const do
     it.PK = ws_get(ctx, WS_MPK, vb * STAG_MAXRHS * STAG_MAXSHIFT);
     it.XK = f64 ? (void*)X : ws_get(ctx, WS_MXK, vb * STAG_MAXRHS * STAG_MAXSHIFT);
     if (!it.R || !it.P || !it.W || !it.T || !it.PK || !it.XK) return stag_fail(ctx, STAG_ERR_OOM, "batched solver workspace");
-    it.chunk = env_i("STAG_CHUNK", 16);
+    it.chunk = env_i("STAG_CHUNK", 32);
     it.tpb = hop_tpb(ctx, lp);
 
     // scalar states and vectors

@@ -27,7 +27,12 @@ namespace {
 
 const int HOP_TPB = 128;
 const int BLAS_TPB = 256;
-const int NR = 4;  // right-hand sides per thread in the multi-RHS hops
+// right-hand sides per thread in the multi-RHS hops: NRMAX while more than
+// two right-hand sides are active, then 2 and 1 (fewer registers, more
+// resident warps for the last, longest-running shifts)
+const int NRMAX = 4;
+const int NR = NRMAX;  // the unfused path
+static int nr_for(int nact) { return nact <= 1 ? 1 : nact <= 2 ? 2 : NRMAX; }
 
 STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
     __shared__ bool am_last;
@@ -42,7 +47,7 @@ STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
     return am_last;
 }
 
-template <int LP>
+template <int LP, int NR = NRMAX>
 __global__ void __launch_bounds__(256, 4) k_b_A(Geom g, const void* __restrict__ U, const float2* __restrict__ P,
                                                  float2* __restrict__ T, size_t stride, BCGState* st) {
     // a stop requested by the previous iteration takes effect here, after that
@@ -212,7 +217,7 @@ __global__ void k_b_D(long n, size_t stride, const float2* __restrict__ R, float
 // right-hand side; its last block computes alpha_k, |r_k - alpha_k w_k|^2 by
 // expansion, beta_k and the parking; CD applies r -= alpha w, x += alpha p and
 // (for right-hand sides still active) p = r + beta p.
-template <int LP>
+template <int LP, int NR = NRMAX>
 __global__ void __launch_bounds__(256, 4) k_b_B3(Geom g, const void* __restrict__ U, const float2* __restrict__ T,
                                                   const float2* __restrict__ P, const float2* __restrict__ R,
                                                   float2* __restrict__ W, size_t stride, BCGState* st,
@@ -424,7 +429,7 @@ struct BIter {
     Links U;
     float2 *R, *P, *W, *T, *XL;
     double* part;
-    int ny_hop, ny_blas, chunk, fused, tpb;
+    int ny_hop, ny_blas, chunk, fused, tpb, nr;
 };
 
 void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
@@ -435,7 +440,15 @@ void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
     const dim3 gh(nblocks(g.Vh, a.tpb), a.ny_hop), gb(ctx->num_sms, a.ny_blas);
     for (int i = 0; i < a.chunk; i++) {
         if (a.fused) {
-            if (a.lp == LP32) {
+            if (a.lp == LP32 && a.nr == 1) {
+                k_b_A<LP32, 1><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+                k_b_B3<LP32, 1><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
+                                                        ctx->gpart, ctx->counter);
+            } else if (a.lp == LP32 && a.nr == 2) {
+                k_b_A<LP32, 2><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
+                k_b_B3<LP32, 2><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
+                                                        ctx->gpart, ctx->counter);
+            } else if (a.lp == LP32) {
                 k_b_A<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
                 k_b_B3<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart,
                                                      ctx->counter);
@@ -483,11 +496,12 @@ int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int 
     it.part = (double*)ws_get(ctx, WS_BPART,
                               sizeof(double) * 4 * STAG_MAXSHIFT * (size_t)(nbx > ctx->num_sms ? nbx : ctx->num_sms));
     if (!it.P || !it.XL || !it.W || !it.T || !it.part) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
+    it.nr = NRMAX;
     it.ny_hop = (nk + NR - 1) / NR;
     it.ny_blas = nk;
-    it.chunk = env_i("STAG_CHUNK", 16);
+    it.chunk = env_i("STAG_CHUNK", 32);
     it.fused = env_i("STAG_FUSED", 1);
-    const double delta = env_d("STAG_RELIABLE_DELTA", 0.1);
+    const double delta = env_d("STAG_RELIABLE_DELTA", 0.03);
     const int trace = env_i("STAG_TRACE_REFINE", 0);
 
     BCGState* hs = ctx->bcg_host;
@@ -514,9 +528,10 @@ int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int 
     while (remaining > 0) {
         // the grids cover the right-hand sides active at the start of the chunk
         // (the device only removes slots within a chunk); one graph per size
-        it.ny_hop = (hs->n_act + NR - 1) / NR;
+        it.nr = (it.fused && lp == LP32 && env_i("STAG_REFINE_NR", 1)) ? nr_for(hs->n_act) : NRMAX;
+        it.ny_hop = (hs->n_act + it.nr - 1) / it.nr;
         it.ny_blas = hs->n_act;
-        snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d", lp, hs->n_act, it.chunk, it.fused, it.tpb);
+        snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d_%d", lp, hs->n_act, it.chunk, it.fused, it.tpb, it.nr);
         int st = run_graph_chunk(ctx, key, (it.fused ? 3 : 4) * it.chunk, enqueue_b, &it, s);
         if (st) return st;
         STAG_CUDA(ctx, cudaMemcpyAsync(hs, ctx->bcg, sizeof(BCGState), cudaMemcpyDeviceToHost, s));

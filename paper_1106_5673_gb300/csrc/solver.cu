@@ -901,13 +901,13 @@ static int ms_reliable_update(stag_ctx* ctx, MSBufs& bf, MSReliable* ru, cudaStr
 
 // Shifted CG with vectors of type R and links LP.  b: FP64 source.  On
 // return the FP64 solutions are in xout (n contiguous vectors).
-// Runs 16-iteration chunks of the shifted CG until the device state stops;
+// Runs chunks of STAG_CHUNK (32) iterations of the shifted CG until the device state stops;
 // with `ru` (FP32 vectors only), a reliable update at every poll that finds
 // the residual reduced by the trigger factor.
 template <typename R, int LP>
 static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s, MSReliable* ru = nullptr) {
     MSState* hs = ctx->ms_host;
-    const int chunk = env_int("STAG_CHUNK", 16);
+    const int chunk = env_int("STAG_CHUNK", 32);
     char key[64];
     snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), hop_tpb(ctx, LP),
              bf.xk);
@@ -1002,7 +1002,7 @@ static int ms_continue(stag_ctx* ctx, double2* xout, const int* ks, int nk, int 
 }
 
 // FP32 shifted CG with reliable updates of the base residual (STAG_MS_RELIABLE=1;
-// trigger factor delta from STAG_RELIABLE_DELTA, 0.1).  Off by default: on the
+// trigger factor delta from STAG_RELIABLE_DELTA, 0.03).  Off by default: on the
 // 32^3x8 workload the base system then follows its true residual to 1e-10
 // (3498 iterations, as in FP64), but the other shifts keep the FP32 floor of
 // their recursion (their residuals are never recomputed) and still need most
@@ -1055,7 +1055,7 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
     ru.b = b;
     ru.X = xout;
     ru.mass = mass;
-    const double delta = env_dbl("STAG_RELIABLE_DELTA", 0.1);
+    const double delta = env_dbl("STAG_RELIABLE_DELTA", 0.03);
     ru.delta2 = delta * delta;
     ru.nupdates = 0;
     if (reliable) STAG_CUDA(ctx, cudaMemsetAsync(xout, 0, sizeof(double2) * n3 * n, s));
@@ -1094,8 +1094,8 @@ int refine_shift(stag_ctx* ctx, double mass, double shift, const double2* b, dou
     if (!r32 || !p32 || !w32 || !t32 || !x32 || !w64 || !t64) return stag_fail(ctx, STAG_ERR_OOM, "refine workspace");
     Links U = make_links(ctx, LP);
     const double c = mass * mass + shift;
-    const double delta = env_dbl("STAG_RELIABLE_DELTA", 0.1);
-    const int chunk = env_int("STAG_CHUNK", 16);
+    const double delta = env_dbl("STAG_RELIABLE_DELTA", 0.03);
+    const int chunk = env_int("STAG_CHUNK", 32);
     int st;
 
     double* dres = ctx->dscal + 0;
