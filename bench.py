@@ -761,8 +761,9 @@ def main():
     ap.add_argument("--roofline-only", action="store_true",
                     help="only time the FP32 hop on the roofline lattice")
     ap.add_argument("--solve-only", action="store_true",
-                    help="one mixed multi-shift solve of the workload's rational on the smooth "
-                         "32^3x8 start (few launches: for kernel profiles)")
+                    help="only the workload's 15-shift mixed solve on 32^3x8 after --therm pure-gauge "
+                         "trajectories (0: the smooth start), repeated --steps times (few launches: "
+                         "for kernel profiles and solver timings)")
     ap.add_argument("--roof-dims", default="64,64,64,16",
                     help="lattice of the large-lattice hop roofline, e.g. 48,48,48,16")
     ap.add_argument("--therm", type=int, default=THERM,
@@ -793,15 +794,23 @@ def main():
     if args.solve_only:
         import torch
         from paper_1106_5673_gb300 import stag, synth
-        _, _, b, _ = stag.remez(-0.5, LO, HI, DEG)
+        a0, a, b, _ = stag.remez(-0.5, LO, HI, DEG)
         L = stag.Lattice(DIMS)
-        L.load_gauge(synth.near_unit_links(DIMS, 0.3, 1))
+        seeds = replica_seeds(0)
+        L.load_gauge(synth.near_unit_links(DIMS, 0.3, seeds["links"]))
+        if args.therm > 0:
+            thermalise(stag, L, (a0, a, b), seeds["therm"], args.therm, beta=THERM_BETA)
         x = torch.from_numpy(synth.gaussian_vector(DIMS, 3)).cuda()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, info = L.multishift_solve(MASS, b, x, tol=TOL, mode=stag.SOLVE_MIXED)
-        torch.cuda.synchronize()
-        print(json.dumps({"solve_only": {"seconds": time.perf_counter() - t0, "iters": info.iters,
+        rows = []
+        for _ in range(max(1, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, info = L.multishift_solve(MASS, b, x, tol=TOL, mode=stag.SOLVE_MIXED)
+            torch.cuda.synchronize()
+            rows.append(time.perf_counter() - t0)
+        print(json.dumps({"solve_only": {"lattice": list(DIMS), "therm": args.therm, "beta_therm": THERM_BETA,
+                                         "plaquette": L.plaquette(), "seconds": rows, "iters": info.iters,
+                                         "iters_shift": list(info.iters_shift[:len(b)]),
                                          "refine_iters": list(info.refine_iters[:len(b)]),
                                          "max_true_resid": max(info.true_resid[:len(b)])}}))
         return 0

@@ -20,6 +20,7 @@
 #include "hop.cuh"
 #include "stag_internal.h"
 
+#include <algorithm>
 #include <math.h>
 #include <stdlib.h>
 
@@ -33,6 +34,11 @@ const int BLAS_TPB = 256;
 const int NRMAX = 4;
 const int NR = NRMAX;  // the unfused path
 static int nr_for(int nact) { return nact <= 1 ? 1 : nact <= 2 ? 2 : NRMAX; }
+// STAG_REFINE_NR: 0 always NRMAX, 1 nr_for (default), 2 one right-hand side
+// per thread, 3 at most two
+static int nr_policy(int nact, int pol) {
+    return pol == 0 ? NRMAX : pol == 2 ? 1 : pol == 3 ? (nact <= 1 ? 1 : 2) : nr_for(nact);
+}
 
 STAG_D bool last_block_n(unsigned int* counter, unsigned int nblocks_total) {
     __shared__ bool am_last;
@@ -429,7 +435,7 @@ struct BIter {
     Links U;
     float2 *R, *P, *W, *T, *XL;
     double* part;
-    int ny_hop, ny_blas, chunk, fused, tpb, nr;
+    int ny_hop, ny_blas, nbx_blas, chunk, fused, tpb, nr;
 };
 
 void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
@@ -437,7 +443,7 @@ void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
     const Geom& g = ctx->g;
     const long n3 = 3L * g.Vh;
     const size_t stride = (size_t)n3;
-    const dim3 gh(nblocks(g.Vh, a.tpb), a.ny_hop), gb(ctx->num_sms, a.ny_blas);
+    const dim3 gh(nblocks(g.Vh, a.tpb), a.ny_hop), gb(a.nbx_blas, a.ny_blas);
     for (int i = 0; i < a.chunk; i++) {
         if (a.fused) {
             if (a.lp == LP32 && a.nr == 1) {
@@ -502,6 +508,8 @@ int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int 
     it.chunk = env_i("STAG_CHUNK", 32);
     it.fused = env_i("STAG_FUSED", 1);
     const double delta = env_d("STAG_RELIABLE_DELTA", 0.03);
+    const int bcd_bps = env_i("STAG_BCD_BPS", 8);
+    it.nbx_blas = ctx->num_sms;
     const int trace = env_i("STAG_TRACE_REFINE", 0);
 
     BCGState* hs = ctx->bcg_host;
@@ -528,10 +536,16 @@ int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int 
     while (remaining > 0) {
         // the grids cover the right-hand sides active at the start of the chunk
         // (the device only removes slots within a chunk); one graph per size
-        it.nr = (it.fused && lp == LP32 && env_i("STAG_REFINE_NR", 1)) ? nr_for(hs->n_act) : NRMAX;
+        it.nr = (it.fused && lp == LP32) ? nr_policy(hs->n_act, env_i("STAG_REFINE_NR", 1)) : NRMAX;
         it.ny_hop = (hs->n_act + it.nr - 1) / it.nr;
         it.ny_blas = hs->n_act;
-        snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d_%d", lp, hs->n_act, it.chunk, it.fused, it.tpb, it.nr);
+        // vector-update blocks per right-hand side: about bcd_bps blocks per SM
+        // over all rows (at least one per SM, at most one float4 per thread)
+        it.nbx_blas = bcd_bps > 0 ? std::max(ctx->num_sms, std::min(nblocks(n3 / 2, BLAS_TPB),
+                                                                     ctx->num_sms * bcd_bps / std::max(1, hs->n_act)))
+                                  : ctx->num_sms;
+        snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d_%d_%d", lp, hs->n_act, it.chunk, it.fused, it.tpb, it.nr,
+                 it.nbx_blas);
         int st = run_graph_chunk(ctx, key, (it.fused ? 3 : 4) * it.chunk, enqueue_b, &it, s);
         if (st) return st;
         STAG_CUDA(ctx, cudaMemcpyAsync(hs, ctx->bcg, sizeof(BCGState), cudaMemcpyDeviceToHost, s));

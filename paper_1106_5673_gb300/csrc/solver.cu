@@ -268,16 +268,25 @@ __global__ void k_ms_CD(long n, long stride, V2* __restrict__ r, const V2* __res
 }
 // FP32 vectors: the same update on float4 (two complex entries per access;
 // 3 Vh is even, so n4 = 3 Vh / 2 and every vector starts 16-byte aligned)
-template <>
-__global__ void k_ms_CD<float2, float>(long n, long stride, float2* __restrict__ r2, const float2* __restrict__ w2,
-                                       float2* __restrict__ p2, float2* __restrict__ pk2, float2* __restrict__ xk2,
-                                       MSState* st, unsigned int* counter) {
+template <int G>
+__global__ void k_ms_CD4(long n, long stride, float2* __restrict__ r2, const float2* __restrict__ w2,
+                         float2* __restrict__ p2, float2* __restrict__ pk2, float2* __restrict__ xk2, MSState* st) {
     if (!st->live) return;
     __shared__ MSCoef<float> c;
+    __shared__ int kl[STAG_MAXSHIFT], nkl;
     ms_load_coef<float>(st, c);
     __syncthreads();
+    // the shifts whose x_k is updated, compacted in order (a ballot over warp 0)
+    if (threadIdx.x < 32) {
+        const int k = threadIdx.x;
+        const bool u = k < STAG_MAXSHIFT && c.ux[k];
+        const unsigned int m = __ballot_sync(0xffffffffu, u);
+        if (u) kl[__popc(m & ((1u << k) - 1u))] = k;
+        if (k == 0) nkl = __popc(m);
+    }
+    __syncthreads();
     const float alpha = (float)st->alpha, beta = (float)st->beta;
-    const int ns = st->n;
+    const int nk = nkl;
     const long n4 = n / 2, s4 = stride / 2;
     float4* r = (float4*)r2;
     const float4* w = (const float4*)w2;
@@ -287,35 +296,49 @@ __global__ void k_ms_CD<float2, float>(long n, long stride, float2* __restrict__
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
         float4 rv = r[i];
         const float4 wv = w[i];
+        float4 pv = p[i];
         rv.x = fmaf(-alpha, wv.x, rv.x);
         rv.y = fmaf(-alpha, wv.y, rv.y);
         rv.z = fmaf(-alpha, wv.z, rv.z);
         rv.w = fmaf(-alpha, wv.w, rv.w);
         r[i] = rv;
-        float4 pv = p[i];
         pv.x = fmaf(beta, pv.x, rv.x);
         pv.y = fmaf(beta, pv.y, rv.y);
         pv.z = fmaf(beta, pv.z, rv.z);
         pv.w = fmaf(beta, pv.w, rv.w);
         p[i] = pv;
-        for (int k = 0; k < ns; k++) {
-            if (!c.ux[k]) continue;
-            float4 q = pk[k * s4 + i];
-            float4 x = xk[k * s4 + i];
-            const float a = c.ak[k];
-            x.x = fmaf(a, q.x, x.x);
-            x.y = fmaf(a, q.y, x.y);
-            x.z = fmaf(a, q.z, x.z);
-            x.w = fmaf(a, q.w, x.w);
-            xk[k * s4 + i] = x;
-            if (c.act[k]) {
-                const float z = c.z[k], b = c.bk[k];
-                q.x = fmaf(b, q.x, z * rv.x);
-                q.y = fmaf(b, q.y, z * rv.y);
-                q.z = fmaf(b, q.z, z * rv.z);
-                q.w = fmaf(b, q.w, z * rv.w);
-                pk[k * s4 + i] = q;
-            }
+        // shifts in groups of G: every load of a group is issued before its
+        // first store (one shift's stores never alias another's loads, which
+        // the compiler cannot prove by itself)
+        for (int j0 = 0; j0 < nk; j0 += G) {
+            float4 q[G], x[G];
+#pragma unroll
+            for (int u = 0; u < G; u++)
+                if (j0 + u < nk) {
+                    const long o = kl[j0 + u] * s4 + i;
+                    q[u] = pk[o];
+                    x[u] = xk[o];
+                }
+#pragma unroll
+            for (int u = 0; u < G; u++)
+                if (j0 + u < nk) {
+                    const int k = kl[j0 + u];
+                    const long o = k * s4 + i;
+                    const float a = c.ak[k];
+                    x[u].x = fmaf(a, q[u].x, x[u].x);
+                    x[u].y = fmaf(a, q[u].y, x[u].y);
+                    x[u].z = fmaf(a, q[u].z, x[u].z);
+                    x[u].w = fmaf(a, q[u].w, x[u].w);
+                    xk[o] = x[u];
+                    if (c.act[k]) {
+                        const float z = c.z[k], b = c.bk[k];
+                        q[u].x = fmaf(b, q[u].x, z * rv.x);
+                        q[u].y = fmaf(b, q[u].y, z * rv.y);
+                        q[u].z = fmaf(b, q[u].z, z * rv.z);
+                        q[u].w = fmaf(b, q[u].w, z * rv.w);
+                        pk[o] = q[u];
+                    }
+                }
         }
     }
 }
@@ -681,6 +704,29 @@ struct MSBufs {
     void *r, *p, *w, *t, *pk, *xk;
 };
 
+// The fused vector update; FP32 vectors take the float4 form with the shifts
+// in groups of STAG_CD_GROUP (1, 2 or 4).  Measured on the 15-shift solve at
+// 32^3x8: 0.155 s with groups of one, 0.156 s with two and 0.157 s with four
+// (the loads issued ahead cost registers and resident warps).
+template <typename V2, typename R>
+static void launch_ms_cd(stag_ctx* ctx, int nb, long n, const MSBufs& b, cudaStream_t s) {
+    if constexpr (sizeof(R) == 4) {
+        const int grp = env_int("STAG_CD_GROUP", 1);
+        if (grp == 1)
+            k_ms_CD4<1><<<nb, BLAS_TPB, 0, s>>>(n, n, (float2*)b.r, (const float2*)b.w, (float2*)b.p, (float2*)b.pk,
+                                                (float2*)b.xk, ctx->ms);
+        else if (grp == 2)
+            k_ms_CD4<2><<<nb, BLAS_TPB, 0, s>>>(n, n, (float2*)b.r, (const float2*)b.w, (float2*)b.p, (float2*)b.pk,
+                                                (float2*)b.xk, ctx->ms);
+        else
+            k_ms_CD4<4><<<nb, BLAS_TPB, 0, s>>>(n, n, (float2*)b.r, (const float2*)b.w, (float2*)b.p, (float2*)b.pk,
+                                                (float2*)b.xk, ctx->ms);
+    } else {
+        k_ms_CD<V2, R><<<nb, BLAS_TPB, 0, s>>>(n, n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, (V2*)b.pk, (V2*)b.xk, ctx->ms,
+                                               ctx->counter);
+    }
+}
+
 template <typename R, int LP>
 void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
     typedef typename VT<R>::T V2;
@@ -689,6 +735,10 @@ void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
     const int tpb = hop_tpb(ctx, LP);
     const int nb_hop = nblocks(g.Vh, tpb);
     const int nb_blas = ctx->num_sms * 4;
+    // the fused vector update: one float4 per thread (3 Vh / 2 of them) by default
+    const int cd_bps = env_int("STAG_CD_BPS", 0);
+    const long n4 = n / 2;
+    const int nb_cd = cd_bps > 0 ? ctx->num_sms * cd_bps : (int)((n4 + BLAS_TPB - 1) / BLAS_TPB);
     if (fused_iter() == 2) {  // deferred shifted updates (A2, B3, C2)
         k_ms_A2<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, (const V2*)b.r, (V2*)b.pk,
                                                  (V2*)b.xk, ctx->ms);
@@ -701,8 +751,7 @@ void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
     if (fused_iter() == 1) {  // shifted updates in the vector kernel (A, B3, CD)
         k_ms_B3<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
                                                  ctx->ms, ctx->partials, ctx->gpart, ctx->counter);
-        k_ms_CD<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, (V2*)b.pk,
-                                                   (V2*)b.xk, ctx->ms, ctx->counter);
+        launch_ms_cd<V2, R>(ctx, nb_cd, n, b, s);
         return;
     }
     k_ms_B<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (V2*)b.w, ctx->ms,
@@ -909,8 +958,8 @@ static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s,
     MSState* hs = ctx->ms_host;
     const int chunk = env_int("STAG_CHUNK", 32);
     char key[64];
-    snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), hop_tpb(ctx, LP),
-             bf.xk);
+    snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), hop_tpb(ctx, LP),
+             env_int("STAG_CD_BPS", 0), env_int("STAG_CD_GROUP", 1), bf.xk);
     int guard = 0, st;
     double rr_max = -1.0;
     auto launch = [&]() {
