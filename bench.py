@@ -205,6 +205,58 @@ def hop_roofline(stag, torch, dims, nrep=30, fmt="f32", L=None):
             "gflops": 570.0 * Vh / t / 1e9, "dims": list(dims), "links": fmt, "bytes_per_site": nb}
 
 
+# algorithmic bytes per output site of the batched refinement's kernels with
+# FP32 12-real links and R right-hand sides: A = D_oe of every p_k (links once,
+# 8 neighbours + 1 output per right-hand side), B3 = D_eo of every t_k with
+# p_k, r_k read and w_k written, CD = r_k, p_k, x_k read and written, w_k read
+def refine_bytes(kernel, R):
+    return {"k_b_A": 384 + R * 216, "k_b_B3": 384 + R * 264, "k_b_CD": R * 168}[kernel]
+
+
+def refine_roofline(stag, torch, dims=(64, 64, 64, 16), nrhs=4, mass=0.0075, shift=1e-4, cupti=True):
+    """The batched refinement's kernels on a lattice whose working set is far
+    above L2: a mixed solve of nrhs equal shifts, so that every refinement
+    launch carries nrhs right-hand sides.  Per kernel: the median of its
+    launches' CUPTI device times (launches issued after convergence inside a
+    graph chunk return at once and fall below the median), algorithmic bytes
+    per launch (refine_bytes x Vh) and their rate against the measured copy
+    peak.  cupti=False runs the same solves without the profiler (for a
+    capture of the same launches under ncu)."""
+    from torch.profiler import ProfilerActivity, profile
+    from paper_1106_5673_gb300 import synth
+    L = stag.Lattice(dims)
+    L.load_gauge(synth.near_unit_links(dims, 0.3, 5))
+    x = torch.from_numpy(synth.gaussian_vector(dims, 6)).cuda()
+    shifts = [shift] * nrhs
+    L.multishift_solve(mass, shifts, x, tol=TOL, mode=stag.SOLVE_MIXED)  # graphs and workspaces
+    torch.cuda.synchronize()
+    if not cupti:
+        _, info = L.multishift_solve(mass, shifts, x, tol=TOL, mode=stag.SOLVE_MIXED)
+        torch.cuda.synchronize()
+        L.close()
+        return {"dims": list(dims), "rhs": nrhs, "refine_iters": list(info.refine_iters[:nrhs])}
+    with profile(activities=[ProfilerActivity.CUDA]) as prof:
+        _, info = L.multishift_solve(mass, shifts, x, tol=TOL, mode=stag.SOLVE_MIXED)
+        torch.cuda.synchronize()
+    durs = {}
+    for e in prof.events():
+        name = _kernel_name(e.name)
+        for kname in ("k_b_A", "k_b_B3", "k_b_CD"):
+            if name == kname or name.startswith(kname + "<"):
+                durs.setdefault(kname, []).append(e.time_range.elapsed_us())
+    Vh = int(np.prod(dims)) // 2
+    peak, kind = _peaks()
+    out = {"dims": list(dims), "rhs": nrhs, "refine_iters": list(info.refine_iters[:nrhs]),
+           "max_true_resid": max(info.true_resid[:nrhs]), "peak_gbs": peak, "peak_kind": kind}
+    for kname, d in durs.items():
+        t = statistics.median(d) * 1e-6
+        nb = refine_bytes(kname, nrhs) * Vh
+        out[kname] = {"launches": len(d), "median_us": t * 1e6, "bytes": nb, "gbs": nb / t / 1e9,
+                      "frac": nb / t / 1e9 / peak}
+    L.close()
+    return out
+
+
 def link_formats(stag, torch, dims):
     """The hop with every link storage on one lattice: 12-real FP32 against
     8-real FP32 (Sec. 4.2's minimal parametrisation) and BF16, and the
@@ -764,6 +816,10 @@ def main():
                     help="only the workload's 15-shift mixed solve on 32^3x8 after --therm pure-gauge "
                          "trajectories (0: the smooth start), repeated --steps times (few launches: "
                          "for kernel profiles and solver timings)")
+    ap.add_argument("--refine-roofline", action="store_true",
+                    help="only time the batched refinement's kernels (four right-hand sides) on the "
+                         "roofline lattice and print them as JSON (with --no-ktable: the same solves "
+                         "without CUPTI, for ncu)")
     ap.add_argument("--roof-dims", default="64,64,64,16",
                     help="lattice of the large-lattice hop roofline, e.g. 48,48,48,16")
     ap.add_argument("--therm", type=int, default=THERM,
@@ -813,6 +869,11 @@ def main():
                                          "iters_shift": list(info.iters_shift[:len(b)]),
                                          "refine_iters": list(info.refine_iters[:len(b)]),
                                          "max_true_resid": max(info.true_resid[:len(b)])}}))
+        return 0
+    if args.refine_roofline:
+        import torch
+        from paper_1106_5673_gb300 import stag
+        print(json.dumps({"refine_roofline": refine_roofline(stag, torch, ROOF_DIMS, cupti=not args.no_ktable)}))
         return 0
     if args.learned_c5:
         import torch
@@ -927,7 +988,7 @@ def main():
             compare.pop("rows")
 
     roof, roof_large, batch, bsolve, learned, revers = None, None, None, None, None, None
-    formats, formats_workload, c2 = None, None, None
+    formats, formats_workload, c2, refine_roof = None, None, None, None
     if not args.no_extras:
         roof = hop_roofline(stag, torch, DIMS)
         formats = _extra(link_formats, stag, torch, ROOF_DIMS)
@@ -936,6 +997,7 @@ def main():
         batch = _extra(batched_hop, stag, torch)
         bsolve = _extra(batched_solve, stag, torch)
         c2 = _extra(c2_solves, stag, torch)
+        refine_roof = _extra(refine_roofline, stag, torch, ROOF_DIMS)
         revers = _extra(reversibility, stag, torch)
         learned = _extra(learned_preconditioner, stag, torch, L, min(rat_act[2]))
     peak, peak_kind = _peaks()
@@ -996,6 +1058,7 @@ def main():
         "batched_hop": batch,
         "batched_solve": bsolve,
         "c2_solves": c2,
+        "refine_roofline": refine_roof,
         "learned_preconditioner": learned,
         "reversibility": revers,
     }
