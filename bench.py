@@ -239,11 +239,13 @@ def refine_roofline(stag, torch, dims=(64, 64, 64, 16), nrhs=4, mass=0.0075, shi
         _, info = L.multishift_solve(mass, shifts, x, tol=TOL, mode=stag.SOLVE_MIXED)
         torch.cuda.synchronize()
     durs = {}
-    for e in prof.events():
-        name = _kernel_name(e.name)
+    for e in prof.profiler.kineto_results.events():  # one record per kernel launch
+        if "CUDA" not in str(e.device_type()):
+            continue
+        name = _kernel_name(e.name())
         for kname in ("k_b_A", "k_b_B3", "k_b_CD"):
             if name == kname or name.startswith(kname + "<"):
-                durs.setdefault(kname, []).append(e.time_range.elapsed_us())
+                durs.setdefault(kname, []).append(e.duration_ns() * 1e-3)
     Vh = int(np.prod(dims)) // 2
     peak, kind = _peaks()
     out = {"dims": list(dims), "rhs": nrhs, "refine_iters": list(info.refine_iters[:nrhs]),
