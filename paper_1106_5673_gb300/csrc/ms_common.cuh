@@ -76,7 +76,7 @@ STAG_D void ms_scalar_update(MSState* st, double t0, double t1, double t2, doubl
         st->beta_old = beta;
         const int bad = !isfinite(rr_new) || !isfinite(beta) || !isfinite(alpha);
         if (bad) st->nonfinite = 1;
-        st->stop_next = (n_active == 0 || iter >= st->maxit || bad) ? 1 : 0;
+        st->stop_next = (n_active <= st->keep || iter >= st->maxit || bad) ? 1 : 0;
         st->pend = 1;
     }
 }

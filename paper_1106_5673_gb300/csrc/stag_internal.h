@@ -49,6 +49,7 @@ struct MSState {
     int n_active;
     int nonfinite;
     int pend;       // 1: the shifted vectors' update of the last iteration is still to be applied
+    int keep;       // stop once at most this many shifts are still unconverged (their refinement finishes them)
 };
 
 // Device-resident scalar state of one single-shift CG with reliable updates.

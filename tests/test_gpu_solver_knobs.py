@@ -11,7 +11,9 @@ Switches (read when a solver chunk's CUDA graph is captured):
 - STAG_BCD_BPS: the refinement's vector-update blocks per SM over all rows
   (0: one block per SM per right-hand side);
 - STAG_REFINE_NR: right-hand sides per thread in the refinement's hops
-  (0 four, 1 by active count, 2 one, 3 at most two).
+  (0 four, 1 by active count, 2 one, 3 at most two);
+- STAG_MS_KEEP: unconverged shifts at which the FP32 shifted CG stops and
+  leaves them to the refinement.
 """
 import numpy as np
 import pytest
@@ -53,6 +55,7 @@ def problem():
     {"STAG_REFINE_NR": "0"},
     {"STAG_REFINE_NR": "2"},
     {"STAG_REFINE_NR": "3"},
+    {"STAG_MS_KEEP": "3"},
 ], ids=lambda e: ",".join("%s=%s" % kv for kv in e.items()))
 def test_mixed_solve_with_launch_switch(S, problem, monkeypatch, env):
     for k, v in env.items():
