@@ -232,6 +232,10 @@ def refine_roofline(stag, torch, dims=(64, 64, 64, 16), nrhs=4, mass=0.0075, shi
     shifts = [shift] * nrhs
     L.multishift_solve(mass, shifts, x, tol=TOL, mode=stag.SOLVE_MIXED)  # graphs and workspaces
     torch.cuda.synchronize()
+    if cupti:  # a first, throw-away profiler session (the first one in a process recorded no kernels here)
+        with profile(activities=[ProfilerActivity.CUDA]):
+            torch.ones(1, device="cuda").add_(1)
+            torch.cuda.synchronize()
     if not cupti:
         _, info = L.multishift_solve(mass, shifts, x, tol=TOL, mode=stag.SOLVE_MIXED)
         torch.cuda.synchronize()
