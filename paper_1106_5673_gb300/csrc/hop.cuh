@@ -244,43 +244,12 @@ STAG_D Vec3<R> hop2(const Geom& g, const void* __restrict__ U, const typename VT
     return acc;
 }
 
-// The same hop with the eight neighbour vectors loaded before any link, so
-// that one thread keeps 8 x 24 bytes of gathers in flight at once: on lattices
-// whose working set sits in L2 the hop is bound by L2 latency with few
-// resident warps (one thread per site), and the extra registers are free.
-template <typename R, int LP>
-STAG_D Vec3<R> hop2_pf(const Geom& g, const void* __restrict__ U, const typename VT<R>::T* __restrict__ in,
-                       int h, int par, const Site& s) {
-    Vec3<R> vf[4], vb[4];
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        vf[mu] = load_vec(in, nb_lex(g, s, mu, +1) >> 1);
-        vb[mu] = load_vec(in, nb_lex(g, s, mu, -1) >> 1);
-    }
-    Vec3<R> acc = vzero<R>();
-#pragma unroll
-    for (int mu = 0; mu < 4; mu++) {
-        int sf = eta(s, mu), sb = sf;
-        if (mu == 3) {
-            if (s.x[3] == g.L[3] - 1) sf = -sf;
-            if (s.x[3] == 0) sb = -sb;
-        }
-        const Mat3<R> uf = get_link<R, LP>(U, g, mu, par, h);
-        mv_acc(acc, uf, vsign((R)sf, vf[mu]));
-        const Mat3<R> ub = get_link<R, LP>(U, g, mu, 1 - par, nb_lex(g, s, mu, -1) >> 1);
-        mdv_acc(acc, ub, vsign((R)(-sb), vb[mu]));
-    }
-    return acc;
-}
-
 // 2 (D psi)(n) with any link precision (R = double for LP64 and LPFF)
-template <typename R, int LP, bool PF = false>
+template <typename R, int LP>
 STAG_D Vec3<R> hopL(const Geom& g, Links L, const typename VT<R>::T* __restrict__ in, int h, int par,
                     const Site& s) {
     if constexpr (LP == LPFF) {
         return hop2_ff(g, (const float4*)L.u, L.lo, in, h, par, s);
-    } else if constexpr (PF) {
-        return hop2_pf<R, LP>(g, L.u, in, h, par, s);
     } else {
         return hop2<R, LP>(g, L.u, in, h, par, s);
     }

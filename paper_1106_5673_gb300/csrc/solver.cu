@@ -41,9 +41,6 @@ static double env_dbl(const char* name, double dflt) {
 // (measured 3 % slower for the FP32 solve at 32^3x8 and 11 % slower in
 // float-float: the streaming does not hide behind the hop's gathers);
 // 0: the four-kernel form A, B, C, D.
-// Neighbour vectors loaded before the links in the shifted CG's hops (STAG_HOP_PF).
-static int hop_pf() { return env_int("STAG_HOP_PF", 0); }
-
 // Unconverged shifts at which the FP32 shifted CG stops (STAG_MS_KEEP,
 // default 0: it runs until every shift has converged).  Measured on the
 // 15-shift solve at 32^3x8: stopping with the lightest 1, 2 or 3 shifts still
@@ -70,7 +67,7 @@ static Links make_links(const stag_ctx* ctx, int lp) {
 
 // ============================================================== multi-shift kernels
 
-template <typename R, int LP, bool PF = false>
+template <typename R, int LP>
 __global__ void __launch_bounds__(256) k_ms_A(Geom g, Links U,
                                                   const typename VT<R>::T* __restrict__ p,
                                                   typename VT<R>::T* __restrict__ t, MSState* st) {
@@ -85,7 +82,7 @@ __global__ void __launch_bounds__(256) k_ms_A(Geom g, Links U,
     const int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= g.Vh) return;
     const Site s = site_of(g, h, 1);
-    Vec3<R> acc = hopL<R, LP, PF>(g, U, p, h, 1, s);
+    Vec3<R> acc = hopL<R, LP>(g, U, p, h, 1, s);
 #pragma unroll
     for (int a = 0; a < 3; a++) acc.c[a] = (R)0.5 * acc.c[a];
     st_vec(t, h, acc);
@@ -160,7 +157,7 @@ __global__ void __launch_bounds__(256) k_ms_B(Geom g, Links U,
 // forms alpha = rr/<p,w> and |r - alpha w|^2 = rr - 2 alpha <r,w> + alpha^2 <w,w>
 // (no separate pass over r), then every scalar of the iteration: the shifted
 // zeta, a_k, b_k, per-shift convergence and the stop flag.
-template <typename R, int LP, bool PF = false>
+template <typename R, int LP>
 __global__ void __launch_bounds__(256) k_ms_B3(Geom g, Links U, const typename VT<R>::T* __restrict__ t,
                                                    const typename VT<R>::T* __restrict__ p,
                                                    const typename VT<R>::T* __restrict__ r,
@@ -175,7 +172,7 @@ __global__ void __launch_bounds__(256) k_ms_B3(Geom g, Links U, const typename V
     R sv[4] = {0, 0, 0, 0};
     if (h < g.Vh) {
         const Site s = site_of(g, h, 0);
-        const Vec3<R> acc = hopL<R, LP, PF>(g, U, t, h, 0, s);
+        const Vec3<R> acc = hopL<R, LP>(g, U, t, h, 0, s);
         const Vec3<R> pv = load_vec(p, h), rv = load_vec(r, h);
         const R c0 = (R)st->c0;
         Vec3<R> wv;
@@ -760,15 +757,6 @@ void launch_ms_iter(stag_ctx* ctx, Links U, const MSBufs& b, cudaStream_t s) {
         k_ms_C2<V2, R><<<nb_blas, BLAS_TPB, 0, s>>>(n, (V2*)b.r, (const V2*)b.w, (V2*)b.p, ctx->ms);
         return;
     }
-    if constexpr (LP == LP32 || LP == LP16) {
-        if (fused_iter() == 1 && hop_pf()) {  // the hops with the neighbour vectors prefetched
-            k_ms_A<R, LP, true><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, ctx->ms);
-            k_ms_B3<R, LP, true><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r,
-                                                       (V2*)b.w, ctx->ms, ctx->partials, ctx->gpart, ctx->counter);
-            launch_ms_cd<V2, R>(ctx, nb_cd, n, b, s);
-            return;
-        }
-    }
     k_ms_A<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.p, (V2*)b.t, ctx->ms);
     if (fused_iter() == 1) {  // shifted updates in the vector kernel (A, B3, CD)
         k_ms_B3<R, LP><<<nb_hop, tpb, 0, s>>>(g, U, (const V2*)b.t, (const V2*)b.p, (const V2*)b.r, (V2*)b.w,
@@ -981,7 +969,7 @@ static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s,
     const int chunk = env_int("STAG_CHUNK", 32);
     char key[64];
     snprintf(key, sizeof key, "ms_%d_%d_%d_%d_%d_%d_%d_%p", (int)sizeof(R), LP, chunk, fused_iter(), hop_tpb(ctx, LP),
-             env_int("STAG_CD_BPS", 0), env_int("STAG_CD_GROUP", 1) + 8 * hop_pf(), bf.xk);
+             env_int("STAG_CD_BPS", 0), env_int("STAG_CD_GROUP", 1), bf.xk);
     int guard = 0, st;
     double rr_max = -1.0;
     auto launch = [&]() {
