@@ -233,14 +233,16 @@ int stag_apply_M_noalloc(const int dims[4], const double *links, double mass, co
 
 /* Batched hop: for each lattice l < nlat (each its own context, all on one
  * device, any sizes), out[l][j] = D_{out_par, 1-out_par} in[l][j] for the
- * nrhs[l] right-hand sides j, all in ONE persistent kernel launch whose
- * blocks walk a list of (lattice, site block, group of right-hand sides)
+ * nrhs[l] right-hand sides j, all in ONE kernel launch whose blocks walk a
+ * list of (lattice, site block, group of right-hand sides)
  * tiles, each link loaded once per tile and applied to the group (Eq. (4)).
  * in[l], out[l]: FP32 complex device vectors [nrhs[l]][V_l/2][3], contiguous
  * (canonical site order of the source and target parity).  prec:
  * STAG_PREC_F32 or STAG_PREC_BF16 links.  The first call for a combination of
- * lattice shapes, nrhs and prec tunes the block size and right-hand sides per
- * thread by timing (synchronises; skipped, with defaults, while `stream` is
+ * lattice shapes, nrhs and prec tunes the block size, the right-hand sides
+ * per thread, the grid form (resident blocks walking the tiles, or one block
+ * per tile) and the tile order by timing (synchronises; skipped, with
+ * defaults, while `stream` is
  * being captured) and caches the choice; tuned_cfg (nullable) receives
  * {threads per block, right-hand sides per thread}.  Otherwise asynchronous;
  * capturable in a CUDA graph.  nlat <= STAG_MAXLAT. */

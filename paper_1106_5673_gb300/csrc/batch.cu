@@ -1,15 +1,19 @@
 // batch.cu -- the even/odd hop of Eq. (4) for many right-hand sides on several
-// lattices of different sizes in one persistent launch.
+// lattices of different sizes in one launch.
 //
 // The work is a list of tiles (lattice, block of output sites, group of NR
-// right-hand sides); each block of the persistent grid walks the list with a
-// grid stride.  Within a tile every link is loaded once and applied to the NR
-// right-hand sides (FP32 vectors, FP32 or BF16 12-real links).  The block
-// size and NR are chosen by a timed search on the first call for each
+// right-hand sides); each block of the grid walks the list with a grid
+// stride (a persistent grid of resident blocks, or one block per tile).
+// Within a tile every link is loaded once and applied to the NR right-hand
+// sides (FP32 vectors, FP32 or BF16 12-real links).  The block size, NR, the
+// grid form and the tile order (site blocks or right-hand-side groups
+// fastest) are chosen by a timed search on the first call for each
 // combination of lattices, right-hand-side counts and link precision, and
 // cached for the process.
 #include <map>
 #include <mutex>
+#include <stdio.h>
+#include <stdlib.h>
 #include <string>
 
 #include "hop.cuh"
@@ -31,6 +35,14 @@ struct BatchLat {
 struct BatchDesc {
     BatchLat l[STAG_MAXLAT];
     int nlat, total_tiles, out_par;
+    int group_fastest;  // tile order within a lattice: 0 site blocks fastest, 1 right-hand-side groups fastest
+};
+
+// launch shape chosen by the tuner: block size, right-hand sides per thread,
+// grid form (0 persistent: resident blocks walk the tiles; 1 one block per
+// tile) and tile order
+struct BatchCfg {
+    int tpb, nr, one_per_tile, group_fastest;
 };
 
 template <int LP, int NR>
@@ -40,7 +52,15 @@ __global__ void __launch_bounds__(256) k_hop_batch(const __grid_constant__ Batch
         while (l + 1 < d.nlat && tile >= d.l[l + 1].tile0) l++;
         const BatchLat& L = d.l[l];
         const int t = tile - L.tile0;
-        const int sb = t % L.nsb, q0 = (t / L.nsb) * NR;
+        int sb, q0;
+        if (d.group_fastest) {
+            const int ng = (L.nrhs + NR - 1) / NR;
+            sb = t / ng;
+            q0 = (t - sb * ng) * NR;
+        } else {
+            sb = t % L.nsb;
+            q0 = (t / L.nsb) * NR;
+        }
         const int h = sb * blockDim.x + threadIdx.x;
         if (h >= L.g.Vh) continue;
         const int nj = min(NR, L.nrhs - q0);
@@ -62,7 +82,7 @@ __global__ void __launch_bounds__(256) k_hop_batch(const __grid_constant__ Batch
 }
 
 template <int LP, int NR>
-int launch_batch(BatchDesc& d, const stag_ctx* const* ctxs, int tpb, int num_sms, cudaStream_t s) {
+int launch_batch(BatchDesc& d, const stag_ctx* const* ctxs, int tpb, int one_per_tile, int num_sms, cudaStream_t s) {
     int tiles = 0;
     for (int l = 0; l < d.nlat; l++) {
         BatchLat& L = d.l[l];
@@ -75,31 +95,33 @@ int launch_batch(BatchDesc& d, const stag_ctx* const* ctxs, int tpb, int num_sms
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hop_batch<LP, NR>, tpb, 0) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    const int grid = (tiles < per_sm * num_sms) ? tiles : per_sm * num_sms;
+    const int grid = (one_per_tile || tiles < per_sm * num_sms) ? tiles : per_sm * num_sms;
     k_hop_batch<LP, NR><<<grid, tpb, 0, s>>>(d);
     (void)ctxs;
     return cudaGetLastError() == cudaSuccess ? STAG_OK : STAG_ERR_CUDA;
 }
 
-int launch_cfg(BatchDesc& d, const stag_ctx* const* ctxs, int lp, int nr, int tpb, int num_sms, cudaStream_t s) {
+int launch_cfg(BatchDesc& d, const stag_ctx* const* ctxs, int lp, const BatchCfg& c, int num_sms, cudaStream_t s) {
+    d.group_fastest = c.group_fastest;
+    const int tpb = c.tpb, opt = c.one_per_tile;
     if (lp == LP16) {
-        switch (nr) {
-            case 1: return launch_batch<LP16, 1>(d, ctxs, tpb, num_sms, s);
-            case 2: return launch_batch<LP16, 2>(d, ctxs, tpb, num_sms, s);
-            case 4: return launch_batch<LP16, 4>(d, ctxs, tpb, num_sms, s);
-            default: return launch_batch<LP16, 8>(d, ctxs, tpb, num_sms, s);
+        switch (c.nr) {
+            case 1: return launch_batch<LP16, 1>(d, ctxs, tpb, opt, num_sms, s);
+            case 2: return launch_batch<LP16, 2>(d, ctxs, tpb, opt, num_sms, s);
+            case 4: return launch_batch<LP16, 4>(d, ctxs, tpb, opt, num_sms, s);
+            default: return launch_batch<LP16, 8>(d, ctxs, tpb, opt, num_sms, s);
         }
     }
-    switch (nr) {
-        case 1: return launch_batch<LP32, 1>(d, ctxs, tpb, num_sms, s);
-        case 2: return launch_batch<LP32, 2>(d, ctxs, tpb, num_sms, s);
-        case 4: return launch_batch<LP32, 4>(d, ctxs, tpb, num_sms, s);
-        default: return launch_batch<LP32, 8>(d, ctxs, tpb, num_sms, s);
+    switch (c.nr) {
+        case 1: return launch_batch<LP32, 1>(d, ctxs, tpb, opt, num_sms, s);
+        case 2: return launch_batch<LP32, 2>(d, ctxs, tpb, opt, num_sms, s);
+        case 4: return launch_batch<LP32, 4>(d, ctxs, tpb, opt, num_sms, s);
+        default: return launch_batch<LP32, 8>(d, ctxs, tpb, opt, num_sms, s);
     }
 }
 
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tuned;  // key -> (tpb, NR)
+std::map<std::string, BatchCfg> g_tuned;  // key -> launch shape
 
 }  // namespace
 
@@ -131,7 +153,7 @@ extern "C" int stag_dslash_batch(int nlat, stag_ctx* const* ctxs, const void* co
         key += "x" + std::to_string(nrhs[l]);
     }
     const int num_sms = ctxs[0]->num_sms;
-    std::pair<int, int> cfg(128, 4);
+    BatchCfg cfg = {128, 4, 0, 0};
     bool have = false;
     {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -144,37 +166,45 @@ extern "C" int stag_dslash_batch(int nlat, stag_ctx* const* ctxs, const void* co
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return stag_cuda_check(ctxs[0], cudaGetLastError(), "stream");
     if (!have && cap == cudaStreamCaptureStatusNone) {
-        // timed search over block size and right-hand sides per thread
+        // timed search over block size, right-hand sides per thread, grid form and tile order
         cudaEvent_t e0, e1;
         if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
             return stag_cuda_check(ctxs[0], cudaGetLastError(), "tuning events");
         const int tpbs[3] = {64, 128, 256}, nrs[4] = {1, 2, 4, 8};
         float best = 1e30f;
-        for (int a = 0; a < 3; a++)
-            for (int b = 0; b < 4; b++) {
-                BatchDesc dd = d;
-                if (launch_cfg(dd, ctxs, lp, nrs[b], tpbs[a], num_sms, s)) return stag_fail(ctxs[0], STAG_ERR_CUDA, "batch tune");
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < 3; r++) launch_cfg(dd, ctxs, lp, nrs[b], tpbs[a], num_sms, s);
-                cudaEventRecord(e1, s);
-                if (cudaEventSynchronize(e1) != cudaSuccess) return stag_cuda_check(ctxs[0], cudaGetLastError(), "tune");
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    cfg = std::make_pair(tpbs[a], nrs[b]);
+        for (int mode = 0; mode < 4; mode++)
+            for (int a = 0; a < 3; a++)
+                for (int b = 0; b < 4; b++) {
+                    const BatchCfg c = {tpbs[a], nrs[b], mode & 1, mode >> 1};
+                    BatchDesc dd = d;
+                    if (launch_cfg(dd, ctxs, lp, c, num_sms, s)) return stag_fail(ctxs[0], STAG_ERR_CUDA, "batch tune");
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < 3; r++) launch_cfg(dd, ctxs, lp, c, num_sms, s);
+                    cudaEventRecord(e1, s);
+                    if (cudaEventSynchronize(e1) != cudaSuccess)
+                        return stag_cuda_check(ctxs[0], cudaGetLastError(), "tune");
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best) {
+                        best = ms;
+                        cfg = c;
+                    }
                 }
-            }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        const char* tr = getenv("STAG_TRACE_BATCH");
+        if (tr && atoi(tr))
+            fprintf(stderr, "[batch] %s: %d threads, %d rhs/thread, %s grid, %s fastest, %.3f ms\n", key.c_str(), cfg.tpb,
+                    cfg.nr, cfg.one_per_tile ? "one block per tile" : "persistent",
+                    cfg.group_fastest ? "rhs groups" : "site blocks", best / 3);
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         g_tuned[key] = cfg;
     }
     if (tuned_cfg) {
-        tuned_cfg[0] = cfg.first;
-        tuned_cfg[1] = cfg.second;
+        tuned_cfg[0] = cfg.tpb;
+        tuned_cfg[1] = cfg.nr;
     }
-    const int st = launch_cfg(d, ctxs, lp, cfg.second, cfg.first, num_sms, s);
+    const int st = launch_cfg(d, ctxs, lp, cfg, num_sms, s);
     ctxs[0]->nlaunch++;
     if (st) return stag_fail(ctxs[0], st, "batched hop launch: %s", cudaGetErrorString(cudaGetLastError()));
     return STAG_OK;
