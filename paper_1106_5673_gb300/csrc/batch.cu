@@ -155,7 +155,20 @@ extern "C" int stag_dslash_batch(int nlat, stag_ctx* const* ctxs, const void* co
     const int num_sms = ctxs[0]->num_sms;
     BatchCfg cfg = {128, 4, 0, 0};
     bool have = false;
-    {
+    // STAG_BATCH_CFG="threads,rhs_per_thread,one_block_per_tile,group_fastest"
+    // forces a launch shape (no search, nothing cached)
+    const char* forced = getenv("STAG_BATCH_CFG");
+    BatchCfg fc;
+    if (forced && sscanf(forced, "%d,%d,%d,%d", &fc.tpb, &fc.nr, &fc.one_per_tile, &fc.group_fastest) == 4) {
+        const bool ok_tpb = fc.tpb == 64 || fc.tpb == 128 || fc.tpb == 256;
+        const bool ok_nr = fc.nr == 1 || fc.nr == 2 || fc.nr == 4 || fc.nr == 8;
+        if (!ok_tpb || !ok_nr) return STAG_ERR_ARG;
+        fc.one_per_tile = fc.one_per_tile != 0;
+        fc.group_fastest = fc.group_fastest != 0;
+        cfg = fc;
+        have = true;
+    }
+    if (!have) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {

@@ -57,6 +57,24 @@ def test_batched_hop_matches_oracle(S, out_par, prec, tol):
                 assert err > 1e-5
 
 
+@pytest.mark.parametrize("shape", ["128,4,0,0", "128,4,1,0", "128,4,0,1", "128,4,1,1", "64,8,1,1", "256,2,0,1",
+                                   "64,1,0,1"])
+def test_batched_hop_every_launch_shape(S, monkeypatch, shape):
+    """Every launch shape the tuner can choose (block size, right-hand sides
+    per thread, persistent grid or one block per tile, site blocks or
+    right-hand-side groups fastest) gives the oracle's hop."""
+    monkeypatch.setenv("STAG_BATCH_CFG", shape)
+    lats, Us, xs = _setup(S, 7)
+    ins = [torch.from_numpy(x).cuda().to(torch.complex64).contiguous() for x in xs]
+    outs, cfg = S.dslash_batch(lats, ins, out_par=1, prec=1)
+    assert list(cfg) == [int(v) for v in shape.split(",")[:2]]
+    torch.cuda.synchronize()
+    for (dims, nr), U, x, y in zip(CASES, Us, xs, outs):
+        y = y.cpu().numpy()
+        for j in range(nr):
+            assert rel(y[j], O.dslash(dims, U, 1, x[j])) < 2e-6, (shape, dims, j)
+
+
 def test_batched_hop_in_cuda_graph(S):
     """After the first (tuning) call the launch is capturable: a CUDA graph
     replayed on new inputs gives the oracle's results."""
