@@ -117,6 +117,10 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
         {(void**)&ctx->counter, counter_bytes},
         {(void**)&ctx->gpart, sizeof(double) * 4 * STAG_MAXSHIFT * ngroups},
         {(void**)&ctx->dscal, sizeof(double) * STAG_NSCAL},
+        {(void**)&ctx->partials2, sizeof(double) * (size_t)maxb},
+        {(void**)&ctx->counter2, counter_bytes},
+        {(void**)&ctx->gpart2, sizeof(double) * 4 * STAG_MAXSHIFT * ngroups},
+        {(void**)&ctx->dscal2, sizeof(double) * STAG_NSCAL},
         {(void**)&ctx->ms, sizeof(MSState)},
         {(void**)&ctx->cg, sizeof(CGState)},
         {(void**)&ctx->bcg, sizeof(BCGState)},
@@ -130,6 +134,10 @@ int stag_ctx_create(const int dims[4], stag_ctx** out) {
         ctx->fixed_bytes += a.bytes;
     }
     if (e == cudaSuccess) e = cudaMemset(ctx->counter, 0, counter_bytes);
+    if (e == cudaSuccess) e = cudaMemset(ctx->counter2, 0, counter_bytes);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->hscal2, sizeof(double) * STAG_NSCAL);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ctx->s2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_ref, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemset(ctx->mom, 0, sizeof(double) * 64 * Vh);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->hscal, sizeof(double) * STAG_NSCAL);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ctx->ms_host, sizeof(MSState));
@@ -154,7 +162,7 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     clear_graphs(ctx);
     void* ps[] = {ctx->U64, ctx->U32, ctx->U32lo, ctx->U16, ctx->U8, ctx->U64_save, ctx->mom, ctx->partials,
                   ctx->counter, ctx->dscal, ctx->ms, ctx->cg, ctx->bcg, ctx->msm, ctx->mm_partials,
-                  ctx->gpart};
+                  ctx->gpart, ctx->partials2, ctx->counter2, ctx->gpart2, ctx->dscal2};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (int i = 0; i < WS_NSLOTS; i++)
@@ -166,6 +174,9 @@ int stag_ctx_destroy(stag_ctx* ctx) {
     if (ctx->msm_host) cudaFreeHost(ctx->msm_host);
     if (ctx->ms_poll) cudaFreeHost(ctx->ms_poll);
     if (ctx->ev_poll) cudaEventDestroy(ctx->ev_poll);
+    if (ctx->hscal2) cudaFreeHost(ctx->hscal2);
+    if (ctx->ev_ref) cudaEventDestroy(ctx->ev_ref);
+    if (ctx->s2) cudaStreamDestroy(ctx->s2);
     delete ctx;
     return STAG_OK;
 }

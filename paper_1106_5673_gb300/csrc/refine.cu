@@ -403,7 +403,8 @@ double env_d(const char* name, double dflt) {
 
 // FP64-accurate residuals r_k = b_k - (M_ee + c_k - m^2) x_k for the listed
 // slots with the float-float operator: FP32 copies into R + k*n3, |r_k|^2
-// into dscal[100 + k] (read back, synchronising).
+// into dscal2[100 + k] (read back, synchronising `s`).  Uses the
+// refinement's own reduction buffers, so it may run beside the shifted CG.
 int batched_true_residuals(stag_ctx* ctx, const RefSlots& S, const int* ks, int nk, float2* R, double* rr_out,
                            cudaStream_t s) {
     const long n3 = 3L * ctx->g.Vh;
@@ -414,15 +415,14 @@ int batched_true_residuals(stag_ctx* ctx, const RefSlots& S, const int* ks, int 
         const int k = ks[i];
         int st = mee_apply(ctx, STAG_PREC_F64FF, S.c[k], S.x[k], w64, t64, s);
         if (st) return st;
-        k_b_residual<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, S.b[k], w64, R + k * n3, ctx->partials, ctx->counter,
-                                                           ctx->dscal + 100 + k);
+        k_b_residual<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, S.b[k], w64, R + k * n3, ctx->partials2,
+                                                           ctx->counter2, ctx->dscal2 + 100 + k);
         STAG_LAUNCH_CHECK(ctx, "batched residual");
     }
-    // scalars 0..100+MAXSHIFT: also brings |b|^2 (slot 1) to the host
-    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal, ctx->dscal, sizeof(double) * (100 + STAG_MAXSHIFT),
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal2 + 100, ctx->dscal2 + 100, sizeof(double) * STAG_MAXSHIFT,
                                    cudaMemcpyDeviceToHost, s));
     STAG_CUDA(ctx, cudaStreamSynchronize(s));
-    for (int i = 0; i < nk; i++) rr_out[ks[i]] = ctx->hscal[100 + ks[i]];
+    for (int i = 0; i < nk; i++) rr_out[ks[i]] = ctx->hscal2[100 + ks[i]];
     return STAG_OK;
 }
 
@@ -449,35 +449,244 @@ void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
             if (a.lp == LP32 && a.nr == 1) {
                 k_b_A<LP32, 1><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
                 k_b_B3<LP32, 1><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
-                                                        ctx->gpart, ctx->counter);
+                                                        ctx->gpart2, ctx->counter2);
             } else if (a.lp == LP32 && a.nr == 2) {
                 k_b_A<LP32, 2><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
                 k_b_B3<LP32, 2><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part,
-                                                        ctx->gpart, ctx->counter);
+                                                        ctx->gpart2, ctx->counter2);
             } else if (a.lp == LP32) {
                 k_b_A<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-                k_b_B3<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart,
-                                                     ctx->counter);
+                k_b_B3<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart2,
+                                                     ctx->counter2);
             } else {
                 k_b_A<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-                k_b_B3<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart,
-                                                     ctx->counter);
+                k_b_B3<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.R, a.W, stride, ctx->bcg, a.part, ctx->gpart2,
+                                                     ctx->counter2);
             }
-            k_b_CD<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, ctx->counter);
+            k_b_CD<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, ctx->counter2);
             continue;
         }
         if (a.lp == LP32) {
             k_b_A<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-            k_b_B<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
+            k_b_B<LP32><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter2);
         } else {
             k_b_A<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.P, a.T, stride, ctx->bcg);
-            k_b_B<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter);
+            k_b_B<LP16><<<gh, a.tpb, 0, cs>>>(g, a.U.u, a.T, a.P, a.W, stride, ctx->bcg, a.part, ctx->counter2);
         }
-        k_b_C<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, a.part, ctx->counter);
-        k_b_D<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.P, ctx->bcg, ctx->counter);
+        k_b_C<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.W, a.P, a.XL, ctx->bcg, a.part, ctx->counter2);
+        k_b_D<<<gb, BLAS_TPB, 0, cs>>>(n3, stride, a.R, a.P, ctx->bcg, ctx->counter2);
     }
 }
 }  // namespace
+
+// ---------------------------------------------------------------- Refiner
+
+int Refiner::begin(stag_ctx* c, int link_prec, const RefSlots* slots, double tolerance, int max_iter, double* rr_io,
+                   int* iters_out, cudaStream_t stream) {
+    ctx = c;
+    lp = link_prec;
+    S = slots;
+    tol = tolerance;
+    maxit = max_iter;
+    rr = rr_io;
+    iters = iters_out;
+    s = stream;
+    const long n3 = 3L * ctx->g.Vh;
+    const size_t vb = sizeof(float2) * n3 * STAG_MAXSHIFT;
+    R = (float2*)ws_get(ctx, WS_BR, vb);
+    P = (float2*)ws_get(ctx, WS_RPK, vb);
+    XL = (float2*)ws_get(ctx, WS_RXL, vb);
+    W = (float2*)ws_get(ctx, WS_BW, vb);
+    T = (float2*)ws_get(ctx, WS_BT, vb);
+    const int nbx = nblocks(ctx->g.Vh, 64);  // partials sized for the smallest block size
+    part = (double*)ws_get(ctx, WS_BPART,
+                           sizeof(double) * 4 * STAG_MAXSHIFT * (size_t)(nbx > ctx->num_sms ? nbx : ctx->num_sms));
+    if (!R || !P || !XL || !W || !T || !part) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
+    tpb = hop_tpb(ctx, lp);
+    chunk = env_i("STAG_CHUNK", 32);
+    fused = env_i("STAG_FUSED", 1);
+    delta = env_d("STAG_RELIABLE_DELTA", 0.03);
+    bcd_bps = env_i("STAG_BCD_BPS", 8);
+    trace = env_i("STAG_TRACE_REFINE", 0);
+    nreliable = nmatvec = 0;
+    norder = remaining = 0;
+    flying = false;
+    for (int k = 0; k < STAG_MAXSHIFT; k++) active[k] = done[k] = 0;
+    BCGState* hs = ctx->bcg_host;
+    memset(hs, 0, sizeof(BCGState));
+    hs->delta2 = delta * delta;
+    hs->maxit = maxit;
+    dirty = true;
+    return STAG_OK;
+}
+
+int Refiner::add(const int* ks, int nk) {
+    if (flying) return stag_fail(ctx, STAG_ERR_STATE, "refinement slots added while a chunk runs");
+    const long n3 = 3L * ctx->g.Vh;
+    BCGState* hs = ctx->bcg_host;
+    for (int i = 0; i < nk; i++) {
+        const int k = ks[i];
+        hs->rr[k] = hs->rr_max[k] = rr[k];
+        hs->c0[k] = S->c[k];
+        hs->tol2bb[k] = tol * tol * S->bb[k];
+        hs->iter[k] = 0;
+        hs->want_rel[k] = 0;
+        STAG_CUDA(ctx, cudaMemsetAsync(XL + k * n3, 0, sizeof(float2) * n3, s));
+        k_b_copy<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, R + k * n3, P + k * n3);
+        STAG_LAUNCH_CHECK(ctx, "refine init");
+        order[norder++] = k;
+        active[k] = 1;
+        remaining++;
+    }
+    // the active list in joining order
+    int na = 0;
+    for (int i = 0; i < norder; i++)
+        if (active[order[i]] && !done[order[i]]) hs->act[na++] = order[i];
+    hs->n_act = na;
+    hs->stop_next = 0;
+    hs->live = na > 0;
+    dirty = true;
+    return STAG_OK;
+}
+
+int Refiner::launch() {
+    BCGState* hs = ctx->bcg_host;
+    if (flying || hs->n_act == 0) return STAG_OK;
+    if (dirty) {
+        STAG_CUDA(ctx, cudaMemcpyAsync(ctx->bcg, hs, sizeof(BCGState), cudaMemcpyHostToDevice, s));
+        dirty = false;
+    }
+    BIter it;
+    it.lp = lp;
+    it.U.u = (lp == LP32) ? (const void*)ctx->U32 : (const void*)ctx->U16;
+    it.U.lo = ctx->U32lo;
+    it.R = R;
+    it.P = P;
+    it.XL = XL;
+    it.W = W;
+    it.T = T;
+    it.part = part;
+    it.tpb = tpb;
+    it.chunk = chunk;
+    it.fused = fused;
+    // the grids cover the right-hand sides active at the start of the chunk
+    // (the device only removes slots within a chunk); one graph per size
+    it.nr = (fused && lp == LP32) ? nr_policy(hs->n_act, env_i("STAG_REFINE_NR", 1)) : NRMAX;
+    it.ny_hop = (hs->n_act + it.nr - 1) / it.nr;
+    it.ny_blas = hs->n_act;
+    // vector-update blocks per right-hand side: about bcd_bps blocks per SM
+    // over all rows (at least one per SM, at most one float4 per thread)
+    const long n3 = 3L * ctx->g.Vh;
+    it.nbx_blas = bcd_bps > 0 ? std::max(ctx->num_sms, std::min(nblocks(n3 / 2, BLAS_TPB),
+                                                                 ctx->num_sms * bcd_bps / std::max(1, hs->n_act)))
+                              : ctx->num_sms;
+    char key[80];
+    snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d_%d_%d", lp, hs->n_act, it.chunk, it.fused, it.tpb, it.nr,
+             it.nbx_blas);
+    int st = run_graph_chunk(ctx, key, (it.fused ? 3 : 4) * it.chunk, enqueue_b, &it, s);
+    if (st) return st;
+    STAG_CUDA(ctx, cudaMemcpyAsync(hs, ctx->bcg, sizeof(BCGState), cudaMemcpyDeviceToHost, s));
+    STAG_CUDA(ctx, cudaEventRecord(ctx->ev_ref, s));
+    flying = true;
+    return STAG_OK;
+}
+
+bool Refiner::ready() const { return !flying || cudaEventQuery(ctx->ev_ref) == cudaSuccess; }
+
+int Refiner::poll() {
+    if (!flying) return STAG_OK;
+    STAG_CUDA(ctx, cudaEventSynchronize(ctx->ev_ref));
+    flying = false;
+    BCGState* hs = ctx->bcg_host;
+    const long n3 = 3L * ctx->g.Vh;
+    if (trace) {
+        fprintf(stderr, "[refine] n_act %d live %d nonfinite %d |", hs->n_act, hs->live, hs->nonfinite);
+        for (int i = 0; i < norder; i++) {
+            const int k = order[i];
+            fprintf(stderr, " k%d it%d rr%.2e a%.2e b%.2e p%d", k, hs->iter[k], hs->rr[k] / S->bb[k], hs->alpha[k],
+                    hs->beta[k], hs->want_rel[k]);
+        }
+        fprintf(stderr, "\n");
+    }
+    if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in batched CG");
+    // reliable updates: parked (claimed convergence) and those whose residual dropped by delta
+    int upd[STAG_MAXSHIFT], nu = 0, parked[STAG_MAXSHIFT] = {0};
+    int in_act[STAG_MAXSHIFT] = {0};
+    for (int a = 0; a < hs->n_act; a++) in_act[hs->act[a]] = 1;
+    for (int i = 0; i < norder; i++) {
+        const int k = order[i];
+        if (done[k]) continue;
+        if (hs->want_rel[k]) {
+            parked[k] = 1;
+            upd[nu++] = k;
+        } else if (in_act[k] && hs->rr[k] > 1e2 * hs->rr_max[k]) {
+            parked[k] = 1;  // the recursion drifted away: restart from the true residual
+            upd[nu++] = k;
+        } else if (in_act[k] && (hs->rr[k] < hs->delta2 * hs->rr_max[k] || hs->iter[k] >= maxit)) {
+            upd[nu++] = k;
+        }
+    }
+    int st;
+    if (nu > 0) {
+        SlotList L;
+        for (int i = 0; i < nu; i++) {
+            L.k[i] = upd[i];
+            L.x[i] = S->x[upd[i]];
+        }
+        k_b_accumulate<<<dim3(ctx->num_sms, nu), BLAS_TPB, 0, s>>>(n3, (size_t)n3, XL, L);
+        STAG_LAUNCH_CHECK(ctx, "refine accumulate");
+        double rrt[STAG_MAXSHIFT];
+        if ((st = batched_true_residuals(ctx, *S, upd, nu, R, rrt, s))) return st;
+        nmatvec += nu;
+        nreliable += nu;
+        for (int i = 0; i < nu; i++) {
+            const int k = upd[i];
+            hs->want_rel[k] = 0;
+            rr[k] = rrt[k];
+            if (rrt[k] <= hs->tol2bb[k] || hs->iter[k] >= maxit) {
+                done[k] = 1;
+                remaining--;
+                in_act[k] = 0;
+                continue;
+            }
+            hs->rr[k] = hs->rr_max[k] = rrt[k];
+            if (parked[k]) {  // the recursion claimed convergence but the true residual disagrees: restart
+                k_b_copy<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, R + k * n3, P + k * n3);
+                STAG_LAUNCH_CHECK(ctx, "refine restart");
+                in_act[k] = 1;
+            }
+        }
+    }
+    // rebuild the active list (compacted, joining order)
+    int na = 0;
+    for (int i = 0; i < norder; i++) {
+        const int k = order[i];
+        active[k] = in_act[k] && !done[k];
+        if (active[k]) hs->act[na++] = k;
+    }
+    hs->n_act = na;
+    hs->stop_next = 0;
+    hs->live = na > 0;
+    dirty = true;
+    if (remaining > 0 && na == 0) return stag_fail(ctx, STAG_ERR_NOCONV, "batched refinement stalled");
+    for (int i = 0; i < norder; i++) iters[order[i]] = hs->iter[order[i]];
+    return STAG_OK;
+}
+
+int Refiner::finish() {
+    int st;
+    while (remaining > 0) {
+        if (!flying && ctx->bcg_host->n_act == 0)
+            return stag_fail(ctx, STAG_ERR_NOCONV, "batched refinement stalled");
+        if ((st = launch())) return st;
+        if ((st = poll())) return st;
+    }
+    for (int i = 0; i < norder; i++) {
+        iters[order[i]] = ctx->bcg_host->iter[order[i]];
+        nmatvec += ctx->bcg_host->iter[order[i]];
+    }
+    return STAG_OK;
+}
 
 // Refines the FP64 solutions S.x[k] of the slots ks[0..nk) (those whose true
 // residual rr[k] > tol^2 bb_k on entry; R + k*n3 must already hold their FP32
@@ -485,139 +694,13 @@ void enqueue_b(stag_ctx* ctx, void* argp, cudaStream_t cs) {
 // residual^2.
 int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int nk, float2* R, double tol, int maxit,
                    double* rr, int* iters, int* reliable, int* matvecs, cudaStream_t s) {
-    const Geom& g = ctx->g;
-    const long n3 = 3L * g.Vh;
-    const size_t vb = sizeof(float2) * n3 * STAG_MAXSHIFT;
-    BIter it;
-    it.lp = lp;
-    it.U.u = (lp == LP32) ? (const void*)ctx->U32 : (const void*)ctx->U16;
-    it.U.lo = ctx->U32lo;
-    it.R = R;
-    it.P = (float2*)ws_get(ctx, WS_PK32, vb);
-    it.XL = (float2*)ws_get(ctx, WS_XK32, vb);
-    it.W = (float2*)ws_get(ctx, WS_BW, vb);
-    it.T = (float2*)ws_get(ctx, WS_BT, vb);
-    it.tpb = hop_tpb(ctx, lp);
-    const int nbx = nblocks(g.Vh, 64);  // partials sized for the smallest block size
-    it.part = (double*)ws_get(ctx, WS_BPART,
-                              sizeof(double) * 4 * STAG_MAXSHIFT * (size_t)(nbx > ctx->num_sms ? nbx : ctx->num_sms));
-    if (!it.P || !it.XL || !it.W || !it.T || !it.part) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
-    it.nr = NRMAX;
-    it.ny_hop = (nk + NR - 1) / NR;
-    it.ny_blas = nk;
-    it.chunk = env_i("STAG_CHUNK", 32);
-    it.fused = env_i("STAG_FUSED", 1);
-    const double delta = env_d("STAG_RELIABLE_DELTA", 0.03);
-    const int bcd_bps = env_i("STAG_BCD_BPS", 8);
-    it.nbx_blas = ctx->num_sms;
-    const int trace = env_i("STAG_TRACE_REFINE", 0);
-
-    BCGState* hs = ctx->bcg_host;
-    memset(hs, 0, sizeof(BCGState));
-    for (int i = 0; i < nk; i++) {
-        const int k = ks[i];
-        hs->act[i] = k;
-        hs->rr[k] = hs->rr_max[k] = rr[k];
-        hs->c0[k] = S.c[k];
-        hs->tol2bb[k] = tol * tol * S.bb[k];
-        STAG_CUDA(ctx, cudaMemsetAsync(it.XL + k * n3, 0, sizeof(float2) * n3, s));
-        k_b_copy<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, R + k * n3, it.P + k * n3);
-        STAG_LAUNCH_CHECK(ctx, "refine init");
-    }
-    hs->n_act = nk;
-    hs->delta2 = delta * delta;
-    hs->maxit = maxit;
-    hs->live = nk > 0;
-    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->bcg, hs, sizeof(BCGState), cudaMemcpyHostToDevice, s));
-
-    char key[64];
-    int remaining = nk;
-    int done[STAG_MAXSHIFT] = {0};
-    while (remaining > 0) {
-        // the grids cover the right-hand sides active at the start of the chunk
-        // (the device only removes slots within a chunk); one graph per size
-        it.nr = (it.fused && lp == LP32) ? nr_policy(hs->n_act, env_i("STAG_REFINE_NR", 1)) : NRMAX;
-        it.ny_hop = (hs->n_act + it.nr - 1) / it.nr;
-        it.ny_blas = hs->n_act;
-        // vector-update blocks per right-hand side: about bcd_bps blocks per SM
-        // over all rows (at least one per SM, at most one float4 per thread)
-        it.nbx_blas = bcd_bps > 0 ? std::max(ctx->num_sms, std::min(nblocks(n3 / 2, BLAS_TPB),
-                                                                     ctx->num_sms * bcd_bps / std::max(1, hs->n_act)))
-                                  : ctx->num_sms;
-        snprintf(key, sizeof key, "bcg_%d_%d_%d_%d_%d_%d_%d", lp, hs->n_act, it.chunk, it.fused, it.tpb, it.nr,
-                 it.nbx_blas);
-        int st = run_graph_chunk(ctx, key, (it.fused ? 3 : 4) * it.chunk, enqueue_b, &it, s);
-        if (st) return st;
-        STAG_CUDA(ctx, cudaMemcpyAsync(hs, ctx->bcg, sizeof(BCGState), cudaMemcpyDeviceToHost, s));
-        STAG_CUDA(ctx, cudaStreamSynchronize(s));
-        if (trace) {
-            fprintf(stderr, "[refine] n_act %d live %d nonfinite %d |", hs->n_act, hs->live, hs->nonfinite);
-            for (int i = 0; i < nk; i++)
-                fprintf(stderr, " k%d it%d rr%.2e a%.2e b%.2e p%d", ks[i], hs->iter[ks[i]], hs->rr[ks[i]] / S.bb[ks[i]],
-                        hs->alpha[ks[i]], hs->beta[ks[i]], hs->want_rel[ks[i]]);
-            fprintf(stderr, "\n");
-        }
-        if (hs->nonfinite) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite residual in batched CG");
-        // reliable updates: parked (claimed convergence) and those whose residual dropped by delta
-        int upd[STAG_MAXSHIFT], nu = 0, parked[STAG_MAXSHIFT] = {0};
-        int in_act[STAG_MAXSHIFT] = {0};
-        for (int a = 0; a < hs->n_act; a++) in_act[hs->act[a]] = 1;
-        for (int i = 0; i < nk; i++) {
-            const int k = ks[i];
-            if (done[k]) continue;
-            if (hs->want_rel[k]) {
-                parked[k] = 1;
-                upd[nu++] = k;
-            } else if (in_act[k] && hs->rr[k] > 1e2 * hs->rr_max[k]) {
-                parked[k] = 1;  // the recursion drifted away: restart from the true residual
-                upd[nu++] = k;
-            } else if (in_act[k] && (hs->rr[k] < hs->delta2 * hs->rr_max[k] || hs->iter[k] >= maxit)) {
-                upd[nu++] = k;
-            }
-        }
-        if (nu > 0) {
-            SlotList L;
-            for (int i = 0; i < nu; i++) {
-                L.k[i] = upd[i];
-                L.x[i] = S.x[upd[i]];
-            }
-            k_b_accumulate<<<dim3(ctx->num_sms, nu), BLAS_TPB, 0, s>>>(n3, (size_t)n3, it.XL, L);
-            STAG_LAUNCH_CHECK(ctx, "refine accumulate");
-            double rrt[STAG_MAXSHIFT];
-            if ((st = batched_true_residuals(ctx, S, upd, nu, R, rrt, s))) return st;
-            *matvecs += nu;
-            *reliable += nu;
-            for (int i = 0; i < nu; i++) {
-                const int k = upd[i];
-                hs->want_rel[k] = 0;
-                rr[k] = rrt[k];
-                if (rrt[k] <= hs->tol2bb[k] || hs->iter[k] >= maxit) {
-                    done[k] = 1;
-                    remaining--;
-                    in_act[k] = 0;
-                    continue;
-                }
-                hs->rr[k] = hs->rr_max[k] = rrt[k];
-                if (parked[k]) {  // the recursion claimed convergence but the true residual disagrees: restart
-                    k_b_copy<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, R + k * n3, it.P + k * n3);
-                    STAG_LAUNCH_CHECK(ctx, "refine restart");
-                    in_act[k] = 1;
-                }
-            }
-        }
-        // rebuild the active list (compacted, stable order)
-        int na = 0;
-        for (int i = 0; i < nk; i++)
-            if (in_act[ks[i]] && !done[ks[i]]) hs->act[na++] = ks[i];
-        hs->n_act = na;
-        hs->stop_next = 0;
-        hs->live = na > 0;
-        if (remaining > 0 && na == 0) return stag_fail(ctx, STAG_ERR_NOCONV, "batched refinement stalled");
-        STAG_CUDA(ctx, cudaMemcpyAsync(ctx->bcg, hs, sizeof(BCGState), cudaMemcpyHostToDevice, s));
-    }
-    for (int i = 0; i < nk; i++) {
-        iters[ks[i]] = hs->iter[ks[i]];
-        *matvecs += hs->iter[ks[i]];
-    }
+    Refiner rf;
+    int st = rf.begin(ctx, lp, &S, tol, maxit, rr, iters, s);
+    if (st) return st;
+    if (rf.R != R) return stag_fail(ctx, STAG_ERR_STATE, "refinement residuals outside the refinement workspace");
+    if ((st = rf.add(ks, nk))) return st;
+    if ((st = rf.finish())) return st;
+    *reliable += rf.nreliable;
+    *matvecs += rf.nmatvec;
     return STAG_OK;
 }

@@ -911,12 +911,14 @@ struct MSReliable {
 
 // Applies the shifted vectors' update that the last iteration left pending
 // (deferred form of the iteration) and clears the flag on the device and in
-// the host mirror.
+// the host mirror.  In the other forms the vector kernel of the iteration has
+// applied it already (the scalar update still raises the flag, which the next
+// B3 clears), so nothing is pending.
 template <typename R>
 static int ms_flush_pending(stag_ctx* ctx, MSBufs& bf, cudaStream_t s) {
     typedef typename VT<R>::T V2;
     MSState* hs = ctx->ms_host;
-    if (!hs->pend) return STAG_OK;
+    if (!hs->pend || fused_iter() != 2) return STAG_OK;
     const long n3 = 3L * ctx->g.Vh;
     k_ms_shift_update<V2, R><<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, n3, (const V2*)bf.r, (V2*)bf.pk, (V2*)bf.xk,
                                                                   ctx->ms);
@@ -960,11 +962,87 @@ static int ms_reliable_update(stag_ctx* ctx, MSBufs& bf, MSReliable* ru, cudaStr
 
 // Shifted CG with vectors of type R and links LP.  b: FP64 source.  On
 // return the FP64 solutions are in xout (n contiguous vectors).
+static int pipeline_on() {
+    static int v = -1;
+    if (v < 0) v = env_int("STAG_PIPELINE", 1);
+    return v;
+}
+static int early_refine_on() { return env_int("STAG_EARLY_REFINE", 0); }
+
+// Early refinement (STAG_EARLY_REFINE=1, mixed modes; off by default): a
+// shift that the FP32 shifted CG has converged is refined at once on the
+// context's second stream, while the shifted CG goes on for the lighter
+// shifts.  At each poll of the shifted CG the hook takes the refinement's
+// finished chunk (without waiting for one still running), hands over the
+// newly converged shifts (x_k is final once the shift is inactive after a
+// whole chunk) and launches the refinement's next chunk.  Measured on the
+// 15-shift solve at 32^3x8 it gains nothing (0.1465 s against 0.146-0.149 s):
+// the two streams' kernels do not fill idle capacity but slow each other
+// (the shifted CG's iteration from 29 to ~42 us, the refinement's chunk of
+// one or two right-hand sides to ~80 us per iteration).
+struct EarlyRef {
+    stag_ctx* ctx = nullptr;
+    Refiner rf;
+    RefSlots S;
+    int n = 0;
+    double tol = 0.0;
+    const float2* xk32 = nullptr;  // the FP32 shifted CG's x_k (stride 3 Vh)
+    int handed[STAG_MAXSHIFT] = {0};
+    double rr[STAG_MAXSHIFT] = {0};
+    int its[STAG_MAXSHIFT] = {0};
+    int nresid = 0;  // true residuals computed at hand-over
+    // copies the listed shifts' x_k to FP64 (after `ev` on the main stream),
+    // computes their true residuals and lets those above tol join the refinement
+    int hand_off(const int* ks, int nk, cudaEvent_t ev) {
+        const long n3 = 3L * ctx->g.Vh;
+        cudaStream_t s2 = ctx->s2;
+        STAG_CUDA(ctx, cudaStreamWaitEvent(s2, ev, 0));
+        int st;
+        for (int i = 0; i < nk; i++)
+            if ((st = blas_copy_f2d(ctx, xk32 + ks[i] * n3, S.x[ks[i]], ctx->g.Vh, s2))) return st;
+        if ((st = batched_true_residuals(ctx, S, ks, nk, rf.R, rr, s2))) return st;
+        nresid += nk;
+        int sel[STAG_MAXSHIFT], ns = 0;
+        for (int i = 0; i < nk; i++) {
+            handed[ks[i]] = 1;
+            if (S.bb[ks[i]] > 0.0 && rr[ks[i]] > tol * tol * S.bb[ks[i]]) sel[ns++] = ks[i];
+        }
+        return ns > 0 ? rf.add(sel, ns) : STAG_OK;
+    }
+    int trace = env_int("STAG_TRACE_EARLY", 0);
+    double t0 = -1.0;
+    double now() {
+        const double t = std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+        if (t0 < 0) t0 = t;
+        return (t - t0) * 1e3;
+    }
+    int on_poll(const MSState* q) {
+        int st;
+        if (trace)
+            fprintf(stderr, "[early] %.3f ms: ms iter %d n_active %d | refine flying %d ready %d n_act %d remaining %d\n",
+                    now(), q->iter, q->n_active, (int)rf.flying, (int)rf.ready(), ctx->bcg_host->n_act, rf.remaining);
+        if (rf.flying) {
+            if (!rf.ready()) return STAG_OK;
+            if ((st = rf.poll())) return st;
+        }
+        if (q->iter > 0) {
+            for (int k = 0; k < n; k++) S.bb[k] = q->bb;
+            int ks[STAG_MAXSHIFT], nk = 0;
+            for (int k = 0; k < n; k++)
+                if (!handed[k] && !q->active[k]) ks[nk++] = k;
+            if (nk > 0 && (st = hand_off(ks, nk, ctx->ev_poll))) return st;
+            if (trace && nk > 0) fprintf(stderr, "[early] %.3f ms: handed over %d shifts\n", now(), nk);
+        }
+        return rf.launch();
+    }
+};
+
 // Runs chunks of STAG_CHUNK (32) iterations of the shifted CG until the device state stops;
 // with `ru` (FP32 vectors only), a reliable update at every poll that finds
 // the residual reduced by the trigger factor.
 template <typename R, int LP>
-static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s, MSReliable* ru = nullptr) {
+static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s, MSReliable* ru = nullptr,
+                  EarlyRef* er = nullptr) {
     MSState* hs = ctx->ms_host;
     const int chunk = env_int("STAG_CHUNK", 32);
     char key[64];
@@ -982,8 +1060,7 @@ static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s,
     // at it, so the GPU does not wait for the host's decision.  A chunk
     // launched after the solve has stopped does nothing (its kernels see the
     // stop flags).  A reliable update waits for the stream and re-reads.
-    static int pipeline = -1;
-    if (pipeline < 0) pipeline = env_int("STAG_PIPELINE", 1);
+    const int pipeline = pipeline_on();
     if ((st = launch())) return st;
     for (;;) {
         const MSState* q = hs;
@@ -996,6 +1073,7 @@ static int ms_run(stag_ctx* ctx, Links U, MSBufs& bf, int maxit, cudaStream_t s,
         } else if ((st = read_ms_state(ctx, s))) {
             return st;
         }
+        if (er && pipeline && !q->nonfinite && (st = er->on_poll(q))) return st;
         if (q->nonfinite || !q->live || q->stop_next) break;
         if (++guard > maxit / chunk + 4) break;  // cannot happen: the device caps iterations
         bool relaunch = !pipeline;
@@ -1081,7 +1159,7 @@ static double ms_tol32(double tol, int lp = LP32) {
 
 template <typename R, int LP>
 int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* b, double2* xout,
-            double tol, int maxit, stag_solve_info* info, cudaStream_t s) {
+            double tol, int maxit, stag_solve_info* info, cudaStream_t s, EarlyRef* er = nullptr) {
     typedef typename VT<R>::T V2;
     const Geom& g = ctx->g;
     const long n3 = 3L * g.Vh;
@@ -1122,7 +1200,8 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
     ru.delta2 = delta * delta;
     ru.nupdates = 0;
     if (reliable) STAG_CUDA(ctx, cudaMemsetAsync(xout, 0, sizeof(double2) * n3 * n, s));
-    if ((st = ms_run<R, LP>(ctx, U, bf, maxit, s, reliable ? &ru : nullptr))) return st;
+    if (er) er->xk32 = (const float2*)bf.xk;
+    if ((st = ms_run<R, LP>(ctx, U, bf, maxit, s, reliable ? &ru : nullptr, er))) return st;
     if (info) {
         info->iters += hs->iter;
         info->matvecs += hs->iter + ru.nupdates;
@@ -1132,8 +1211,67 @@ int ms_core(stag_ctx* ctx, double mass, int n, const double* shifts, const doubl
     if (reliable) {  // the increments since the last update
         k_ms_flush<<<ctx->num_sms * 4, BLAS_TPB, 0, s>>>(n3, n3, n, (float2*)bf.xk, xout);
         STAG_LAUNCH_CHECK(ctx, "ms flush");
-    } else if (!f64) {
+    } else if (!f64 && !er) {  // (the early refinement copies each shift as it takes it over)
         if ((st = blas_copy_f2d(ctx, (const float2*)bf.xk, xout, (long)g.Vh * n, s))) return st;
+    }
+    return STAG_OK;
+}
+
+// The mixed solve with early refinement: the FP32 shifted CG on `s`, the
+// batched refinement of each shift from the moment the shifted CG has
+// converged it on the second stream, then the remaining (lightest) shifts.
+// Fills info like finish_batched; *status is STAG_OK or STAG_ERR_NOCONV.
+template <int LP>
+static int mixed_early(stag_ctx* ctx, double mass, int n, const double* shifts, const double2* src, double2* X,
+                       double tol, int maxit, stag_solve_info* info, cudaStream_t s, int* status) {
+    const long n3 = 3L * ctx->g.Vh;
+    EarlyRef er;
+    er.ctx = ctx;
+    er.n = n;
+    er.tol = tol;
+    for (int k = 0; k < n; k++) {
+        er.S.b[k] = src;
+        er.S.x[k] = X + k * n3;
+        er.S.c[k] = mass * mass + shifts[k];
+        er.S.bb[k] = 0.0;
+    }
+    // every buffer the refinement touches exists before the shifted CG starts
+    if (!ws_get(ctx, WS_W64, sizeof(double2) * n3) || !ws_get(ctx, WS_T64, sizeof(double2) * n3))
+        return stag_fail(ctx, STAG_ERR_OOM, "residual workspace");
+    // the refinement uses FP32 links in every mixed mode (see finish_batched)
+    int st = er.rf.begin(ctx, LP32, &er.S, tol, maxit, er.rr, er.its, ctx->s2);
+    if (st) return st;
+    const double tol32 = (LP == LP16) ? ms_tol32(tol, LP16) : ms_tol32(tol);
+    st = ms_core<float, LP>(ctx, mass, n, shifts, src, X, tol32, maxit, info, s, &er);
+    if (!st && er.rf.flying) st = er.rf.poll();
+    if (!st) {  // the rest, after the shifted CG's last chunk
+        const double bb = ctx->ms_host->bb;
+        for (int k = 0; k < n; k++) er.S.bb[k] = bb;
+        int ks[STAG_MAXSHIFT], nk = 0;
+        for (int k = 0; k < n; k++)
+            if (!er.handed[k]) ks[nk++] = k;
+        STAG_CUDA(ctx, cudaEventRecord(ctx->ev_poll, s));
+        if (nk > 0) st = er.hand_off(ks, nk, ctx->ev_poll);
+    }
+    if (er.trace) fprintf(stderr, "[early] %.3f ms: shifted CG done, %d slots still refining\n", er.now(), er.rf.remaining);
+    if (!st) st = er.rf.finish();
+    if (er.trace) fprintf(stderr, "[early] %.3f ms: refinement done\n", er.now());
+    if (st) {
+        cudaStreamSynchronize(ctx->s2);
+        return st;
+    }
+    // the caller's stream sees the refined solutions
+    STAG_CUDA(ctx, cudaEventRecord(ctx->ev_ref, ctx->s2));
+    STAG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_ref, 0));
+    const double bb = er.S.bb[0];
+    info->reliable_updates += er.rf.nreliable;
+    info->matvecs += er.rf.nmatvec + er.nresid;
+    *status = STAG_OK;
+    for (int k = 0; k < n; k++) {
+        info->refine_iters[k] = er.its[k];
+        info->true_resid[k] = (bb > 0.0) ? sqrt(er.rr[k] / bb) : 0.0;
+        if (!isfinite(info->true_resid[k])) return stag_fail(ctx, STAG_ERR_NONFINITE, "non-finite solution");
+        if (er.rr[k] > tol * tol * bb * 1.0000001) *status = STAG_ERR_NOCONV;
     }
     return STAG_OK;
 }
@@ -1245,6 +1383,8 @@ static int finish_batched(stag_ctx* ctx, double mass, int n, const double* shift
     if (!R) return stag_fail(ctx, STAG_ERR_OOM, "refinement workspace");
     int st;
     if ((st = blas_dot_re(ctx, STAG_PREC_F64, src, src, ctx->dscal + 1, s))) return st;
+    // |b|^2 to the host (the residuals below synchronise the stream)
+    STAG_CUDA(ctx, cudaMemcpyAsync(ctx->hscal + 1, ctx->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     RefSlots S;
     int all[STAG_MAXSHIFT];
     for (int k = 0; k < n; k++) {
@@ -1369,6 +1509,8 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
         if ((st = autotune_hops(ctx, s))) return st;
     }
     const int check_prec = (mode == STAG_SOLVE_F64) ? STAG_PREC_F64 : STAG_PREC_F64FF;
+    bool early = false;
+    int early_status = STAG_OK;
     if (mode == STAG_SOLVE_F64) {
         st = ms_core<double, LP64>(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
     } else if (mode == STAG_SOLVE_F64FF) {
@@ -1380,7 +1522,13 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
         // refinement keeps the 12-real FP32 links)
         static int r8 = -1;
         if (r8 < 0) r8 = env_int("STAG_MS_LINKS8", 0);
-        if (mode == STAG_SOLVE_MIXED && r8) {
+        early = env_int("STAG_BATCHED", 1) && early_refine_on() && fused_iter() == 1 && pipeline_on() &&
+                !ms_reliable_on() && !(mode == STAG_SOLVE_MIXED && r8);
+        if (early && mode == STAG_SOLVE_MIXED)
+            st = mixed_early<LP32>(ctx, mass, n, shifts, src, X, tol, maxit, info, s, &early_status);
+        else if (early)
+            st = mixed_early<LP16>(ctx, mass, n, shifts, src, X, tol, maxit, info, s, &early_status);
+        else if (mode == STAG_SOLVE_MIXED && r8) {
             if (!links_r8(ctx, s)) return STAG_ERR_OOM;
             st = ms_core<float, LP8>(ctx, mass, n, shifts, src, X, ms_tol32(tol), maxit, info, s);
         } else if (mode == STAG_SOLVE_MIXED)
@@ -1394,9 +1542,9 @@ int multishift_solve(stag_ctx* ctx, double mass, int n, const double* shifts, co
 
     const int batched = (mode == STAG_SOLVE_MIXED || mode == STAG_SOLVE_MIXED_BF16) && env_int("STAG_BATCHED", 1);
     if (batched || mode == STAG_SOLVE_LEARNED) {
-        int status = (mode == STAG_SOLVE_LEARNED)
-                         ? learned_solve(ctx, mass, n, shifts, src, X, tol, maxit, info, s)
-                         : finish_batched(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
+        int status = (mode == STAG_SOLVE_LEARNED) ? learned_solve(ctx, mass, n, shifts, src, X, tol, maxit, info, s)
+                     : early                      ? early_status
+                                                  : finish_batched(ctx, mass, n, shifts, src, X, tol, maxit, info, s);
         if (status && status != STAG_ERR_NOCONV) return status;
         if (sols) {
             for (int k = 0; k < n; k++)

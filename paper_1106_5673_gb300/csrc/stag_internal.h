@@ -34,6 +34,7 @@ enum WsSlot {
     WS_MPK, WS_MXK, WS_MX,                // per-system shifted p_k / x_k (low precision), FP64 solutions
     WS_FCG,                               // flexible CG vectors
     WS_LX,                                // learned mode: solution of the lightest shift
+    WS_RPK, WS_RXL,                       // batched refinement: search directions, FP32 corrections
     WS_NSLOTS
 };
 
@@ -91,6 +92,15 @@ struct stag_ctx {
     double* gpart;      // group sums of grid_reduce_series
     double* dscal;      // device scalar area (STAG_NSCAL doubles)
     double* hscal;      // pinned host mirror of dscal
+    // the batched refinement's own reduction buffers and scalars, so that it
+    // can run on the second stream while the shifted CG runs on the first
+    double* partials2;
+    unsigned int* counter2;
+    double* gpart2;
+    double* dscal2;
+    double* hscal2;
+    cudaStream_t s2;      // second stream (the early refinement)
+    cudaEvent_t ev_ref;   // end of the refinement's chunk in flight and of its state copy
     MSState* ms;        // device multi-shift state
     MSState* ms_host;   // pinned host mirror
     MSState* ms_poll;   // pinned copy read one chunk behind (pipelined polling)
@@ -189,6 +199,39 @@ int batched_true_residuals(stag_ctx* ctx, const RefSlots& S, const int* ks, int 
                            cudaStream_t s);
 int refine_batched(stag_ctx* ctx, int lp, const RefSlots& S, const int* ks, int nk, float2* R, double tol, int maxit,
                    double* rr, int* iters, int* reliable, int* matvecs, cudaStream_t s);
+
+// The batched refinement driven chunk by chunk: slots can join while it runs
+// (add), a chunk runs asynchronously on `s` (launch), and the host processes
+// it when it has finished (ready, poll: reliable updates, parking, the active
+// list).  refine_batched is begin + add + finish on one stream; the mixed
+// shifted solve also uses it on the context's second stream, where shifts
+// start their refinement as soon as the FP32 shifted CG has converged them.
+struct Refiner {
+    stag_ctx* ctx = nullptr;
+    cudaStream_t s = 0;
+    int lp = 1;
+    const RefSlots* S = nullptr;
+    double tol = 0.0;
+    int maxit = 0;
+    double* rr = nullptr;  // per slot: the latest FP64-accurate true residual^2 (caller's array)
+    int* iters = nullptr;  // per slot: iterations of its refinement (caller's array)
+    int nreliable = 0, nmatvec = 0;
+    float2 *R = nullptr, *P = nullptr, *W = nullptr, *T = nullptr, *XL = nullptr;
+    double* part = nullptr;
+    int chunk = 32, fused = 1, tpb = 128, bcd_bps = 8, trace = 0;
+    double delta = 0.03;
+    int active[STAG_MAXSHIFT] = {0}, done[STAG_MAXSHIFT] = {0};
+    int order[STAG_MAXSHIFT] = {0}, norder = 0;  // slots in the order they joined
+    int remaining = 0;
+    bool flying = false, dirty = false;
+    int begin(stag_ctx* c, int link_prec, const RefSlots* slots, double tolerance, int max_iter, double* rr_io,
+              int* iters_out, cudaStream_t stream);
+    int add(const int* ks, int nk);  // the slots' rows of R and rr[] hold their true residuals (above tol)
+    int launch();                    // one chunk, asynchronous (no-op when no slot is active)
+    bool ready() const;              // the chunk in flight has finished
+    int poll();                      // processes the finished chunk (waits for it first)
+    int finish();                    // runs until every slot has met tol or its iteration cap
+};
 
 // ---------------------------------------------------------------- msmulti.cu
 int multishift_solve_multi(stag_ctx* ctx, double mass, int nsys, int n, const double* shifts,

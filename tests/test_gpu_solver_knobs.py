@@ -13,7 +13,9 @@ Switches (read when a solver chunk's CUDA graph is captured):
 - STAG_REFINE_NR: right-hand sides per thread in the refinement's hops
   (0 four, 1 by active count, 2 one, 3 at most two);
 - STAG_MS_KEEP: unconverged shifts at which the FP32 shifted CG stops and
-  leaves them to the refinement.
+  leaves them to the refinement;
+- STAG_EARLY_REFINE: converged shifts start their refinement on a second
+  stream while the FP32 shifted CG goes on.
 """
 import numpy as np
 import pytest
@@ -56,6 +58,8 @@ def problem():
     {"STAG_REFINE_NR": "2"},
     {"STAG_REFINE_NR": "3"},
     {"STAG_MS_KEEP": "3"},
+    {"STAG_EARLY_REFINE": "1"},
+    {"STAG_EARLY_REFINE": "1", "STAG_REFINE_NR": "0"},
 ], ids=lambda e: ",".join("%s=%s" % kv for kv in e.items()))
 def test_mixed_solve_with_launch_switch(S, problem, monkeypatch, env):
     for k, v in env.items():
