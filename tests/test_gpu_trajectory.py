@@ -215,19 +215,28 @@ def test_md_reversibility_fp64_and_mixed(S, rationals):
     assert dC[S.SOLVE_MIXED] > dC[S.SOLVE_F64]
 
 
-def test_trajectory_full_size_32x32x32x8_f64(S):
-    """The bench's lattice, mass and rationals (degree 15 on [1e-5, 64]), one
-    short leapfrog step (tau 0.005) from the smooth start, FP64 mode: heatbath, actions,
-    forces, updates and the Metropolis decision against the oracle at full
-    size (the oracle's solves on the smooth field take seconds)."""
-    dims = (32, 32, 32, 8)
+FULL = (32, 32, 32, 8)
+
+
+@pytest.fixture(scope="module")
+def full_size_oracle(S):
+    """The oracle's trajectory at the bench's lattice, mass and rationals
+    (degree 15 on [1e-5, 64]): one short leapfrog step (tau 0.005) from the
+    smooth start (its solves on the smooth field take seconds)."""
     a = S.remez(-0.5, 1e-5, 64.0, 15)[:3]
     h = S.remez(0.25, 1e-5, 64.0, 15)[:3]
-    U = synth.near_unit_links(dims, 0.3, 1)
+    U = synth.near_unit_links(FULL, 0.3, 1)
     po = O.make_params(5.5, 0.0075, 0.005, 1, 0, h, a, a, tol_md=1e-10, tol_metro=1e-10, seed=3, traj=4)
-    Uo, io, st = O.trajectory(dims, U, po)
+    Uo, io, st = O.trajectory(FULL, U, po)
     assert st == 0 and io["accepted"] == 1  # a step short enough to be kept: the links moved
-    L = S.Lattice(dims)
+    return a, h, U, Uo, io
+
+
+def test_trajectory_full_size_32x32x32x8_f64(S, full_size_oracle):
+    """FP64 mode at full size: heatbath, actions, forces, updates and the
+    Metropolis decision against the oracle."""
+    a, h, U, Uo, io = full_size_oracle
+    L = S.Lattice(FULL)
     L.load_gauge(U)
     ig = L.md_trajectory(S.make_params(5.5, 0.0075, 0.005, 1, 0, h, a, a, tol_md=1e-10, tol_metro=1e-10,
                                        mode_md=S.SOLVE_F64, mode_metro=S.SOLVE_F64, seed=3, traj=4))
@@ -235,3 +244,21 @@ def test_trajectory_full_size_32x32x32x8_f64(S):
     assert abs(ig["H0"] - io["H0"]) < 1e-10 * abs(io["H0"])
     assert abs(ig["dH"] - io["dH"]) < 1e-6
     assert np.abs(L.store_gauge() - Uo).max() < 1e-10
+
+
+def test_trajectory_full_size_32x32x32x8_mixed(S, full_size_oracle):
+    """The bench's mode (FP32 shifted CG, batched refinement, FP32 gauge
+    force; every solve 1e-10 FP64-accurate) at full size against the oracle:
+    the same accept decision, H0 to 1e-9 relative (the heatbath and action
+    solves meet 1e-10 by another path than the oracle's, as on 16^3 x 4),
+    dH within the mixed tolerance 1e-7 sqrt(N_dof) with N_dof = 32 V, and
+    links within 1e-7."""
+    a, h, U, Uo, io = full_size_oracle
+    L = S.Lattice(FULL)
+    L.load_gauge(U)
+    ig = L.md_trajectory(S.make_params(5.5, 0.0075, 0.005, 1, 0, h, a, a, tol_md=1e-10, tol_metro=1e-10,
+                                       mode_md=S.SOLVE_MIXED, mode_metro=S.SOLVE_MIXED, seed=3, traj=4))
+    assert ig["accepted"] == io["accepted"]
+    assert abs(ig["H0"] - io["H0"]) < 1e-9 * abs(io["H0"])
+    assert abs(ig["dH"] - io["dH"]) < 1e-7 * np.sqrt(32 * np.prod(FULL))
+    assert np.abs(L.store_gauge() - Uo).max() < 1e-7
