@@ -1,6 +1,6 @@
 """The slab decomposition along t (Sec. 5.2) on CPU ranks: index maps and
 halo ranges bit for bit, and D_oe, D_eo, M_ee and a CG over the split
-against the single-domain oracle, with two gloo ranks (the local operator on
+against the single-domain oracle, with two and four gloo ranks (the local operator on
 each rank is the oracle's hop on its padded lattice; the decomposition's own
 code does the partitioning, the halo exchange and the reductions)."""
 import os
@@ -90,9 +90,11 @@ def _worker(rank, world, port, q):
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_match_the_single_domain_oracle():
+@pytest.mark.parametrize("world", [2, 4])
+def test_gloo_ranks_match_the_single_domain_oracle(world):
+    """Two ranks (each rank's lower and upper neighbour is the same rank)
+    and four (all different), slabs of 4 and 2 time slices."""
     import oracle as O
-    world = 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
